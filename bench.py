@@ -1,0 +1,338 @@
+"""Throughput of the adaptive-AB3 extended Boussinesq step on GB300.
+
+One bench step = one full time step of the hot path (controller + ghost
+cells, KP07 fluxes + dispersive terms + AB3 combine, y-line and x-line
+tridiagonal solves, sponge, CFL reduction) over one domain.
+
+Default workload: the barred beach with three rip channels, 2048 x 2048 cells,
+FP32 with compensated accumulation (the large single-domain configuration;
+its working set, ~0.5 GB, is far larger than the 129 MB L2, so no L2 flush is
+needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, bounded sample
+
+Under torchrun each rank advances its own replica domain on its own GPU (no
+data exchange); ``value`` is the sum over ranks of cell-updates / the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1909_04153_gb300 import workloads as W  # noqa: E402
+
+METRIC = "cell-updates/s"
+N_KERNELS = 5
+# algorithmic bytes per interior cell of each kernel (values it must read +
+# write once), per precision; the whole step in STEP_VALUES
+KERNEL_VALUES = {"fp32": {"rhs_combine": 21, "ysolve": 8, "xsolve": 11},
+                 "fp64": {"rhs_combine": 19, "ysolve": 6, "xsolve": 9}}
+STEP_VALUES = {"fp32": 25, "fp64": 19}
+
+
+def make_case(workload, n):
+    if workload == "barred_beach":
+        return W.barred_beach(nx=n, ny=n)
+    if workload == "planar_beach":
+        return W.planar_beach(nx=n, ny=max(4, n // 4))
+    raise ValueError(workload)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(f) > 5 + k and f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if os.environ.get("BSQ_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(v, pg, device=None):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, pg, device=None):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_rate(case, seconds, max_steps=10 ** 9):
+    """Cell-updates/s of the FP64 CPU oracle on one case, for about `seconds`."""
+    import oracle
+
+    p = case["params"]
+    o = oracle.OracleDomain(p, case["bed"], case["comps"], case["eta0"], case["P0"], case["Q0"])
+    o.step()  # warm
+    n, t0 = 0, time.perf_counter()
+    while n < max_steps:
+        rc = o.step()
+        if rc:
+            raise RuntimeError("oracle step failed %d" % rc)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    return p["nx"] * p["ny"] * n / el, n, el
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup()
+    if rank != 0:
+        return 0
+    # each step: one oracle time step of a bounded sample of the workload (the
+    # same layout on a coarser grid), sized so that warmup + steps take ~2 min
+    import oracle
+
+    probe = make_case(args.workload, 128)
+    rate, _, _ = oracle_rate(probe, 3.0)
+    budget = 120.0
+    cells = max(32 * 32, min(args.n * args.n, rate * budget / max(1, args.steps + args.warmup)))
+    n = int(max(32, min(args.n, math.sqrt(cells))))
+    case = make_case(args.workload, n)
+    p = case["params"]
+    o = oracle.OracleDomain(p, case["bed"], case["comps"], case["eta0"], case["P0"], case["Q0"])
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc = o.step()
+        if rc:
+            raise RuntimeError("oracle step failed %d" % rc)
+    el = time.perf_counter() - t0
+    value = p["nx"] * p["ny"] * args.steps / el
+    sample = "%s %dx%d (same layout, coarser grid), FP64, one oracle step per bench step" % (
+        args.workload, p["nx"], p["ny"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s_%dx%d" % (args.workload, args.n, args.n), "sample_grid": [p["nx"], p["ny"]]},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1909_04153_gb300 import bsq
+
+    world, rank, local, pg = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    case = make_case(args.workload, args.n)
+    p = case["params"]
+    ncell = p["nx"] * p["ny"]
+    prec = args.precision
+    fp = "fp32" if prec == "fp32" else "fp64"
+    dom = bsq.Domain(case, precision=prec, kahan=(prec == "fp32"), stream=stream.cuda_stream,
+                     graph_steps=args.graph_steps)
+    # warm-up (also builds the CUDA graph)
+    dom.advance(max_steps=args.warmup)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as ck:
+        e0.record(stream)
+        n = dom.advance(max_steps=args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if n != args.steps:
+        raise RuntimeError("took %d of %d steps" % (n, args.steps))
+    ms = e0.elapsed_time(e1)
+    if pg is not None:
+        pg.barrier()
+    ms_max = max_over_ranks(ms, pg, dev if pg is not None else None)
+    total_cells = sum_over_ranks(float(ncell), pg, dev if pg is not None else None)
+    value = total_cells * args.steps / (ms_max * 1e-3)
+    clocks = ck.summary()
+
+    # per-kernel durations, live, with CUDA events on the library's stream
+    kms = dom.profile_kernels(args.profile_steps)
+    top = max(("rhs_combine", "ysolve", "xsolve"), key=lambda k: kms[k])
+    esize = 4 if fp == "fp32" else 8
+    alg_bytes = KERNEL_VALUES[fp][top] * esize * ncell
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kms[top] * 1e-3) / 1e9
+    step_bytes = STEP_VALUES[fp] * esize
+    step_achieved = value / world * step_bytes / 1e9
+    info = dom.info()
+    dom.close()
+
+    # end to end through the C ABI with host buffers: create (uploads the
+    # bathymetry and initial state), advance, read eta back
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d2 = bsq.Domain(case, precision=prec, kahan=(prec == "fp32"), stream=stream.cuda_stream,
+                    graph_steps=args.graph_steps)
+    d2.advance(max_steps=args.steps)
+    eta = d2.read("eta")
+    t_e2e = time.perf_counter() - t0
+    d2.close()
+    t_e2e = max_over_ranks(t_e2e, pg, dev if pg is not None else None)
+    h2d = 8 * ((p["nx"] + 1) * (p["ny"] + 1) + (3 if case["eta0"] is not None else 0) * ncell)
+    e2e = {"value": total_cells * args.steps / t_e2e, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": eta.nbytes / args.steps,
+           "includes": "bsq_create from host arrays + bsq_advance + bsq_read(eta)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # bounded sample: the same layout on a 256 x 256 grid, ~15 s of oracle work
+        rate, nst, el = oracle_rate(make_case(args.workload, 256), 15.0)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": "%s 256x256 (same layout, coarser grid), %d FP64 steps in %.1f s, one thread" % (
+                   args.workload, nst, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s_%dx%d" % (args.workload, p["nx"], p["ny"]), "precision": prec,
+                       "kahan": prec == "fp32", "cross_mode": "sequential", "cfl": p["cfl"],
+                       "cells": ncell, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set %.0f MB > 129 MB L2, no flush" % (
+                           bsq_bytes_estimate(ncell, fp) / 1e6)},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": None, "bytes_per_cell": KERNEL_VALUES[fp][top] * esize},
+            "step_roofline": {"bytes_per_cell_update": step_bytes, "achieved": step_achieved,
+                              "frac": step_achieved / peak, "peak": peak},
+            "kernel_ms": kms,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": N_KERNELS * args.graph_steps * math.ceil(args.steps / args.graph_steps) + 1,
+            "clocks": clocks,
+            "sim": {"t": info["t"], "clamps": info["clamps"]},
+        }
+        print(json.dumps(line))
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def bsq_bytes_estimate(ncell, fp):
+    return ncell * (31 if fp == "fp32" else 28) * (4 if fp == "fp32" else 8)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="barred_beach", choices=["barred_beach", "planar_beach"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--graph-steps", type=int, default=16)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

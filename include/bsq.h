@@ -1,0 +1,175 @@
+/*
+ * bsq.h -- C ABI of the GB300 (sm_103a) extended Boussinesq solver with
+ * variable-step third-order Adams-Bashforth time stepping
+ * (Tavakkol, Son & Lynett, arXiv 1909.04153).
+ *
+ * One call advances a domain: the 2D Madsen-Sorensen equations (Sec. 2,
+ * Eqs. 1-3) in the Wei-Kirby form (Sec. 3.1, Eqs. 6-15) on a uniform grid with
+ * two ghost layers per side (Sec. 3.3), hyperbolic part by the central-upwind
+ * scheme of Kurganov-Petrova (Sec. 3), dispersive part by central differences,
+ * P and Q recovered from tridiagonal line systems (Eqs. 19-21), the step size
+ * from the CFL rule (Eq. 22) with the lazy moving average (Eq. 47), and the
+ * variable-step AB3 update (Eqs. 42-46).
+ *
+ * Conventions
+ *   - Every call returns a bsq_status; no call aborts the process.
+ *   - Inputs are copied; outputs go to caller-owned buffers.
+ *   - Host arrays are row-major with x fastest: element (i, j) at i + j*nx.
+ *   - A domain handle is not thread-safe; all its work runs on one CUDA stream.
+ *   - The first error is sticky: later calls on that domain return it until
+ *     bsq_destroy.
+ *   - Waits for the device are bounded (bsq_params.timeout_s) and end with
+ *     BSQ_ERR_TIMEOUT; no call spins forever.
+ *   - The library allocates its device memory with cudaMalloc at bsq_create
+ *     and frees it in bsq_destroy; bsq_advance and bsq_step_dt allocate nothing.
+ */
+#ifndef BSQ_H
+#define BSQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsq_domain bsq_domain;
+
+typedef enum {
+    BSQ_OK = 0,
+    BSQ_ERR_ARG = 1,        /* invalid argument or size */
+    BSQ_ERR_OOM = 2,        /* device or host allocation failed */
+    BSQ_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    BSQ_ERR_NONFINITE = 4,  /* a non-finite value appeared in the state */
+    BSQ_ERR_UNSTABLE = 5,   /* the CFL step fell below dt_min */
+    BSQ_ERR_TIMEOUT = 6,    /* a bounded wait for the device ran out */
+    BSQ_ERR_STATE = 7       /* call not valid in the current state */
+} bsq_status;
+
+enum { BSQ_FP32 = 0, BSQ_FP64 = 1 };
+
+/* Boundary types per side (Sec. 3.3).  A sponge side is a reflective wall
+ * with an absorbing band of width sponge_width inside the domain. */
+enum { BSQ_BC_WALL = 0, BSQ_BC_SPONGE = 1, BSQ_BC_MAKER = 2 };
+
+/* Sides, in this order, in bsq_boundary.type and sponge_width. */
+enum { BSQ_WEST = 0, BSQ_EAST = 1, BSQ_SOUTH = 2, BSQ_NORTH = 3 };
+
+/* Fields for bsq_read. ETA = h - d with h = max(w - b, 0), d = max(w_s - b, 0). */
+enum { BSQ_FIELD_ETA = 0, BSQ_FIELD_P = 1, BSQ_FIELD_Q = 2, BSQ_FIELD_H = 3, BSQ_FIELD_W = 4 };
+
+/* Cross-term forms for the time derivatives of F*(Q) and G*(P) (Eqs. 7-8).
+ * EXTRAPOLATED: both extrapolated in time with the variable-step differences
+ *   of Eqs. 44-46 inside Eq. 43, exactly as printed (Eqs. 17-18 at fixed step);
+ *   unstable in 2D once the still depth exceeds about 1.5 grid cells.
+ * SEQUENTIAL (default): G* as printed; Q^{n+1} is solved first and F* is
+ *   evaluated at the new level from Q^{n+1}; stable at any depth. */
+enum { BSQ_CROSS_EXTRAPOLATED = 0, BSQ_CROSS_SEQUENTIAL = 1 };
+
+typedef struct {
+    int nx, ny;            /* interior cells; 3 <= nx, ny <= 16384 */
+    double dx, dy;         /* cell sizes (m) */
+    double g;              /* gravity, 9.81 */
+    double Bd;             /* dispersion coefficient B of Eqs. 2-3, 1/15 */
+    double cfl;            /* target CFL of Eq. 22 */
+    double ema_alpha;      /* alpha of Eq. 47 (0 < alpha <= 1) */
+    double dt_init;        /* first step; <= 0: from Eq. 22 */
+    double dt_min;         /* a CFL step below this is BSQ_ERR_UNSTABLE */
+    double dt_max;         /* upper clamp; <= 0: none */
+    double friction;       /* quadratic bottom friction factor f (f1 = f u |u|) */
+    double theta;          /* generalized minmod parameter, 1 = minmod (Sec. 3.4) */
+    double eps;            /* desingularisation epsilon; <= 0: max(dx,dy)^4 */
+    double w_s;            /* still water elevation above the datum */
+    double ramp_time;      /* wave maker ramp r(t) = tanh(3 t / ramp_time); <= 0: none */
+    double timeout_s;      /* bound of each host wait for the device; <= 0: 600 s */
+    int precision;         /* BSQ_FP32 or BSQ_FP64 */
+    int kahan;             /* FP32: compensated accumulation of w, P, Q increments */
+    int cross_mode;        /* BSQ_CROSS_* */
+    int graph_steps;       /* steps per captured CUDA graph in bsq_advance; <= 0: 16 */
+} bsq_params;
+
+typedef struct {
+    int type[4];               /* BSQ_BC_* per side W, E, S, N */
+    double sponge_width[4];    /* band width (m) of sponge sides */
+    int n_comp;                /* wave-maker components (0 if no maker side) */
+    const double *amp;         /* amplitude (m) */
+    const double *freq;        /* frequency (Hz) */
+    const double *phase;       /* phase (rad) */
+    const double *dir;         /* direction of travel (rad, 0 = +x) */
+} bsq_boundary;
+
+/* Fill *p with the defaults (g 9.81, Bd 1/15, cfl 0.125, alpha 0.1, theta 1,
+ * FP32 with Kahan, sequential cross terms); nx, ny, dx, dy are left zero. */
+void bsq_params_default(bsq_params *p);
+
+/* Create a domain (Sec. 3.3 grid with two ghost layers per side).
+ *   bed_corners: (nx+1)*(ny+1) bed elevations at cell corners, corner (i,j) at
+ *                (i dx, j dy); mirrored outward for the ghost cells; copied.
+ *   bnd:         boundary spec; NULL = walls on all sides; arrays copied.
+ *   eta0, P0, Q0: nx*ny initial surface (eta = h - d) and fluxes, or NULL (0).
+ *                The initial depth is h = max(d + eta0, 0).
+ *   cuda_stream: cudaStream_t to run on; NULL = a stream the library creates.
+ *   out:         receives the handle; owned by the caller until bsq_destroy.
+ * Errors: BSQ_ERR_ARG (bad sizes, tridiagonal rows not diagonally dominant),
+ * BSQ_ERR_OOM, BSQ_ERR_CUDA.  On error *out is NULL. */
+bsq_status bsq_create(const bsq_params *p, const double *bed_corners, const bsq_boundary *bnd,
+                      const double *eta0, const double *P0, const double *Q0,
+                      void *cuda_stream, bsq_domain **out);
+
+/* Advance with adaptive steps (Eqs. 22, 47) until t = t_end (the last step is
+ * clamped to land on t_end) or max_steps more steps were taken (<= 0: no
+ * limit).  *steps_done (may be NULL) receives the number taken.  Runs captured
+ * CUDA graphs of graph_steps steps; steps past the end inside a graph do no
+ * work.  Errors: BSQ_ERR_NONFINITE, BSQ_ERR_UNSTABLE, BSQ_ERR_TIMEOUT,
+ * BSQ_ERR_CUDA. */
+bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done);
+
+/* Take n steps with the given step sizes dts[0..n-1] (host array), instead of
+ * the CFL rule: replays a recorded dt sequence. */
+bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n);
+
+/* Copy one field of the interior (BSQ_FIELD_*) to host_out (nx*ny doubles,
+ * caller-owned).  FP32 values are widened to double.  Waits for the domain's
+ * stream (bounded). */
+bsq_status bsq_read(const bsq_domain *d, int field, double *host_out);
+
+/* Copy one field of the interior to device memory dev_out (nx*ny elements of
+ * the domain's precision, caller-owned), enqueued on the domain's stream. */
+bsq_status bsq_read_device(const bsq_domain *d, int field, void *dev_out);
+
+/* Simulated time, steps taken, last step size, mass sum(h) dx dy and the
+ * number of positivity clamps (w raised to b after an update) so far.
+ * Any pointer may be NULL.  Waits for the domain's stream (bounded). */
+bsq_status bsq_info(const bsq_domain *d, double *t, long long *n, double *last_dt, double *mass,
+                    long long *clamps);
+
+/* Checkpoint: with buf NULL, *len receives the size needed.  Otherwise writes
+ * the full state (fields, compensation terms, AB3 history, step sizes, time)
+ * into buf (*len bytes available) and sets *len.  Restore puts it back into a
+ * domain created with the same parameters; the continued run is bitwise the
+ * same as one that was never interrupted. */
+bsq_status bsq_checkpoint(const bsq_domain *d, void *buf, size_t *len);
+bsq_status bsq_restore(bsq_domain *d, const void *buf, size_t len);
+
+/* Release everything; NULL-safe. */
+void bsq_destroy(bsq_domain *d);
+
+/* Static text for a status code. */
+const char *bsq_status_string(bsq_status s);
+
+/* Device bytes held by the domain (state, history, scratch, static fields). */
+size_t bsq_device_bytes(const bsq_domain *d);
+
+/* Kernel timing: takes n_steps adaptive steps kernel by kernel (no graph),
+ * with CUDA events recorded on the domain's stream around every launch, and
+ * writes the mean duration (ms) of each kernel of the step to ms_out[k]
+ * (ms_out holds at least 8 doubles); *n_kernels receives the number of
+ * kernels and bsq_kernel_name(k) their names.  The steps are real steps:
+ * the simulation advances by n_steps. */
+bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels);
+const char *bsq_kernel_name(int k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSQ_H */

@@ -35,7 +35,11 @@
  *   - Tridiagonal boundary rows: wall = odd mirror of the normal flux;
  *     wave maker = prescribed ghost value moved to the right-hand side.
  *   - Sponge: gamma(r) = 1/2 + 1/2 cos(pi (1 - r/L)), r from the outer edge,
- *     eta, P, Q scaled by gamma once per step after the solves.
+ *     product over sponge sides; eta, P, Q scaled by gamma once per step,
+ *     Q right after its solve, eta and P after the P solve.
+ *   - cross_mode 1 (default): the y-lines are solved first and F* is taken
+ *     at the new level from Q^{n+1}; cross_mode 0 extrapolates F* and G* as
+ *     printed in Eqs. 17-18 / 43.
  *   - Wave maker: linear components eta = r(t) sum a cos(k.x - w t + phi),
  *     flux = (omega/k) eta along the direction of travel,
  *     r(t) = tanh(3 t / ramp_time), k from the linearised dispersion relation.
@@ -755,6 +759,12 @@ int orc_step(orc_dom *D, double dt_replay, double t_end)
         orc_thomas(ny, D->ta, D->tb, D->tc, D->tr, D->tx);
         for (int j = 0; j < ny; j++) D->Q[CI(D, i, j)] = D->tx[j];
     }
+    /* sponge on Q (Sec. 3.3): Q scaled by gamma as soon as Q^{n+1} exists */
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double gm = D->sponge[CI(D, i, j)];
+            if (gm < 1.0) D->Q[CI(D, i, j)] *= gm;
+        }
 
     if (!fs_extrap) {
         /* F* of Eq. 14 at the new level from Q^{n+1} (ghosts at t_{n+1}) */
@@ -801,7 +811,7 @@ int orc_step(orc_dom *D, double dt_replay, double t_end)
         for (int i = 0; i < nx; i++) D->P[CI(D, i, j)] = D->tx[i];
     }
 
-    /* sponge layers: eta, P, Q scaled by gamma */
+    /* sponge on eta and P once P^{n+1} exists */
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int c = CI(D, i, j);
@@ -810,7 +820,6 @@ int orc_step(orc_dom *D, double dt_replay, double t_end)
                 double h = fmax(D->w[c] - D->b[c], 0.0), d = D->d[c];
                 D->w[c] = D->b[c] + (d + gm * (h - d));
                 D->P[c] *= gm;
-                D->Q[c] *= gm;
             }
         }
 

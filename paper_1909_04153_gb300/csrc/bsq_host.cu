@@ -1,0 +1,766 @@
+// bsq_host.cu -- host engine and C ABI (include/bsq.h) of the GB300 extended
+// Boussinesq solver with variable-step AB3 time stepping (arXiv 1909.04153).
+//
+// bsq_create prepares everything that does not change in time: the bed at
+// cell corners and centres (KP07 layout, Sec. 3), the still depth d and its
+// gradients, the tridiagonal rows of Eqs. 19-21 with their boundary rows and
+// their Thomas factors (the matrices depend on d only, so they are factored
+// once), the sponge profiles and the wave-maker components.  bsq_advance then
+// runs captured CUDA graphs of whole steps; the only host-device traffic per
+// graph is the launch and a 64-byte status read.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/bsq.h"
+#include "bsq_internal.cuh"
+#include "bsq_launch.h"
+
+using namespace bsq;
+
+struct bsq_domain {
+    bsq_params p;
+    bsq_boundary bnd;
+    int fp64;
+    int nx, ny, hx, pitch, rows;
+    long long fstride;
+    cudaStream_t stream;
+    int own_stream;
+    void *dmem;
+    size_t dbytes;
+    Ctl *ctl;
+    Coef *coef;
+    double *mass_partial;
+    int mass_blocks;
+    Ctl *h_ctl;  // pinned
+    Dev<float> Df;
+    Dev<double> Dd;
+    cudaGraphExec_t graph;
+    int graph_steps;
+    bsq_status sticky;
+    int n_state_fields;  // fields saved by a checkpoint
+};
+
+static const char *kStatus[] = {"ok", "invalid argument", "out of memory", "CUDA error",
+                                "non-finite value in the state", "unstable: CFL step below dt_min",
+                                "timed out waiting for the device", "invalid state"};
+
+extern "C" const char *bsq_status_string(bsq_status s)
+{
+    if ((int)s < 0 || (int)s > 7) return "unknown status";
+    return kStatus[(int)s];
+}
+
+extern "C" void bsq_params_default(bsq_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->g = 9.81;
+    p->Bd = 1.0 / 15.0;
+    p->cfl = 0.125;
+    p->ema_alpha = 0.1;
+    p->dt_min = 1e-9;
+    p->theta = 1.0;
+    p->timeout_s = 600.0;
+    p->precision = BSQ_FP32;
+    p->kahan = 1;
+    p->cross_mode = BSQ_CROSS_SEQUENTIAL;
+    p->graph_steps = 16;
+}
+
+#define CK(call)                                     \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) {                     \
+            return BSQ_ERR_CUDA;                     \
+        }                                            \
+    } while (0)
+
+static bsq_status set_sticky(bsq_domain *d, bsq_status s)
+{
+    if (d && d->sticky == BSQ_OK && s != BSQ_OK) d->sticky = s;
+    return s;
+}
+
+// Bounded wait for the domain's stream (limit_s <= 0: the domain's timeout).
+static bsq_status wait_stream(const bsq_domain *d, double limit_s = 0.0)
+{
+    double lim = limit_s > 0 ? limit_s : (d->p.timeout_s > 0 ? d->p.timeout_s : 600.0);
+    auto t0 = std::chrono::steady_clock::now();
+    int us = 20;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(d->stream);
+        if (e == cudaSuccess) return BSQ_OK;
+        if (e != cudaErrorNotReady) return BSQ_ERR_CUDA;
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > lim) return BSQ_ERR_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(us));
+        if (us < 1000) us *= 2;
+    }
+}
+
+// Linearised dispersion relation of Eqs. 1-3 over still depth d:
+// omega^2 = g d k^2 (1 + B (kd)^2) / (1 + (B + 1/3)(kd)^2); bisection on k
+// (the right side increases with k).
+static double wave_number(double omega, double d, double g, double B)
+{
+    if (omega <= 0.0 || d <= 0.0) return 0.0;
+    auto f = [&](double k) {
+        double kd2 = k * d * k * d;
+        return g * d * k * k * (1.0 + B * kd2) / (1.0 + (B + 1.0 / 3.0) * kd2) - omega * omega;
+    };
+    double lo = 0.0, hi = omega / sqrt(g * d);
+    while (f(hi) < 0.0) hi *= 2.0;
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (f(mid) < 0.0) lo = mid; else hi = mid;
+        if (hi - lo <= 1e-16 * hi) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+template <typename T>
+static Dev<T> &dev_of(bsq_domain *d);
+template <>
+Dev<float> &dev_of<float>(bsq_domain *d) { return d->Df; }
+template <>
+Dev<double> &dev_of<double>(bsq_domain *d) { return d->Dd; }
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------ create
+
+template <typename T>
+static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0, const double *P0,
+                           const double *Q0)
+{
+    const bsq_params &p = dm->p;
+    const int nx = p.nx, ny = p.ny;
+    const int hx = 16 / (int)sizeof(T);
+    const int seg = row_segment<T>();
+    const int pitch = ((nx + seg - 1) / seg) * seg + seg;  // covers hx + last segment + 1
+    const int rows = ny + 4;
+    const long long fs = (long long)pitch * rows;
+    // field stride: padded field rounded up to 256 bytes (the history ring is
+    // indexed with this stride)
+    const long long fstride = (long long)(align256((size_t)fs * sizeof(T)) / sizeof(T));
+    dm->hx = hx;
+    dm->pitch = pitch;
+    dm->rows = rows;
+    dm->fstride = fstride;
+    if (!step_shape_ok<T>(nx, ny)) return BSQ_ERR_ARG;
+    const bool kahan = p.kahan && sizeof(T) == 4;
+    dm->p.kahan = kahan ? 1 : 0;
+
+    // ---- static geometry in FP64 on the host
+    const int cx = nx + 5, cy = ny + 5;
+    std::vector<double> corner((size_t)cx * cy);
+    for (int j = -2; j <= ny + 2; j++) {
+        int js = j < 0 ? -j : (j > ny ? 2 * ny - j : j);
+        for (int i = -2; i <= nx + 2; i++) {
+            int is = i < 0 ? -i : (i > nx ? 2 * nx - i : i);
+            corner[(size_t)(j + 2) * cx + (i + 2)] = bed[(size_t)is + (size_t)js * (nx + 1)];
+        }
+    }
+    auto K = [&](int i, int j) { return corner[(size_t)(j + 2) * cx + (i + 2)]; };
+    auto cidx = [&](int i, int j) { return (size_t)(j + 2) * pitch + (i + hx); };
+    std::vector<double> bC((size_t)fs, 0.0), dd((size_t)fs, 0.0);
+    for (int j = -2; j <= ny + 1; j++)
+        for (int i = -2; i <= nx + 1; i++) {
+            double bw = 0.5 * (K(i, j) + K(i, j + 1)), be = 0.5 * (K(i + 1, j) + K(i + 1, j + 1));
+            double bs = 0.5 * (K(i, j) + K(i + 1, j)), bn = 0.5 * (K(i, j + 1) + K(i + 1, j + 1));
+            double b = 0.25 * (bw + be + bs + bn);
+            bC[cidx(i, j)] = b;
+            dd[cidx(i, j)] = fmax(p.w_s - b, 0.0);
+        }
+    auto D_ = [&](int i, int j) { return dd[cidx(i, j)]; };
+    const double kB = p.Bd + 1.0 / 3.0;
+    // Eq. 21 coefficients of one cell, x and y
+    auto coefx = [&](int i, int j, double &A, double &B, double &C) {
+        double d = D_(i, j), gx = (D_(i + 1, j) - D_(i - 1, j)) / (2.0 * p.dx);
+        A = d * gx / (6.0 * p.dx) - kB * d * d / (p.dx * p.dx);
+        B = 1.0 + 2.0 * kB * d * d / (p.dx * p.dx);
+        C = -d * gx / (6.0 * p.dx) - kB * d * d / (p.dx * p.dx);
+    };
+    auto coefy = [&](int i, int j, double &A, double &B, double &C) {
+        double d = D_(i, j), gy = (D_(i, j + 1) - D_(i, j - 1)) / (2.0 * p.dy);
+        A = d * gy / (6.0 * p.dy) - kB * d * d / (p.dy * p.dy);
+        B = 1.0 + 2.0 * kB * d * d / (p.dy * p.dy);
+        C = -d * gy / (6.0 * p.dy) - kB * d * d / (p.dy * p.dy);
+    };
+    const int *bt = dm->bnd.type;
+    // Thomas factors per line with the boundary rows closed: wall/sponge =
+    // odd mirror of the normal flux (diagonal minus the outside coefficient),
+    // maker = outside value known (moved to the right-hand side each step).
+    std::vector<T> fxm((size_t)fs, (T)0), fxe((size_t)fs, (T)1), fxc((size_t)fs, (T)0);
+    std::vector<T> fym((size_t)fs, (T)0), fye((size_t)fs, (T)1), fyc((size_t)fs, (T)0);
+    std::vector<double> cW(ny), cE(ny), cS(nx), cN(nx);
+    for (int j = 0; j < ny; j++) {
+        double cprev = 0.0;
+        for (int i = 0; i < nx; i++) {
+            double A, B, C;
+            coefx(i, j, A, B, C);
+            if (i == 0) { cW[j] = A; if (bt[BSQ_WEST] != BSQ_BC_MAKER) B -= A; A = 0.0; }
+            if (i == nx - 1) { cE[j] = C; if (bt[BSQ_EAST] != BSQ_BC_MAKER) B -= C; C = 0.0; }
+            if (!(fabs(B) > fabs(A) + fabs(C))) return BSQ_ERR_ARG;
+            double den = B - A * cprev;
+            double m = 1.0 / den;
+            cprev = C * m;
+            fxm[cidx(i, j)] = (T)m;
+            fxe[cidx(i, j)] = (T)(-A * m);
+            fxc[cidx(i, j)] = (T)cprev;
+        }
+    }
+    for (int i = 0; i < nx; i++) {
+        double cprev = 0.0;
+        for (int j = 0; j < ny; j++) {
+            double A, B, C;
+            coefy(i, j, A, B, C);
+            if (j == 0) { cS[i] = A; if (bt[BSQ_SOUTH] != BSQ_BC_MAKER) B -= A; A = 0.0; }
+            if (j == ny - 1) { cN[i] = C; if (bt[BSQ_NORTH] != BSQ_BC_MAKER) B -= C; C = 0.0; }
+            if (!(fabs(B) > fabs(A) + fabs(C))) return BSQ_ERR_ARG;
+            double den = B - A * cprev;
+            double m = 1.0 / den;
+            cprev = C * m;
+            fym[cidx(i, j)] = (T)m;
+            fye[cidx(i, j)] = (T)(-A * m);
+            fyc[cidx(i, j)] = (T)cprev;
+        }
+    }
+    // sponge profiles: gamma(r) = 1/2 + 1/2 cos(pi (1 - r/L)) inside a band of
+    // width L, r from the outer edge; product over sponge sides
+    auto sg = [](double r, double L) {
+        if (L <= 0.0 || r >= L) return 1.0;
+        if (r < 0.0) r = 0.0;
+        return 0.5 + 0.5 * cos(M_PI * (1.0 - r / L));
+    };
+    std::vector<T> gx(nx), gy(ny);
+    for (int i = 0; i < nx; i++) {
+        double g = 1.0;
+        if (bt[BSQ_WEST] == BSQ_BC_SPONGE) g *= sg((i + 0.5) * p.dx, dm->bnd.sponge_width[BSQ_WEST]);
+        if (bt[BSQ_EAST] == BSQ_BC_SPONGE) g *= sg((nx - i - 0.5) * p.dx, dm->bnd.sponge_width[BSQ_EAST]);
+        gx[i] = (T)g;
+    }
+    for (int j = 0; j < ny; j++) {
+        double g = 1.0;
+        if (bt[BSQ_SOUTH] == BSQ_BC_SPONGE) g *= sg((j + 0.5) * p.dy, dm->bnd.sponge_width[BSQ_SOUTH]);
+        if (bt[BSQ_NORTH] == BSQ_BC_SPONGE) g *= sg((ny - j - 0.5) * p.dy, dm->bnd.sponge_width[BSQ_NORTH]);
+        gy[j] = (T)g;
+    }
+    // wave-maker components at the still depth of the first maker side
+    int nc = dm->bnd.n_comp;
+    bool anymaker = false;
+    for (int s = 0; s < 4; s++) anymaker |= bt[s] == BSQ_BC_MAKER;
+    if (!anymaker) nc = 0;
+    double dmk = 0.0;
+    for (int s = 0; s < 4; s++) {
+        if (bt[s] != BSQ_BC_MAKER) continue;
+        int i = s == BSQ_WEST ? -1 : (s == BSQ_EAST ? nx : nx / 2);
+        int j = s == BSQ_SOUTH ? -1 : (s == BSQ_NORTH ? ny : ny / 2);
+        dmk = D_(i, j);
+        break;
+    }
+    std::vector<double> comp((size_t)7 * (nc > 0 ? nc : 1), 0.0);
+    for (int k = 0; k < nc; k++) {
+        double om = 2.0 * M_PI * dm->bnd.freq[k];
+        double kw = wave_number(om, dmk, p.g, p.Bd);
+        double th = dm->bnd.dir[k];
+        double c = kw > 0.0 ? om / kw : 0.0;
+        comp[0 * nc + k] = dm->bnd.amp[k];
+        comp[1 * nc + k] = om;
+        comp[2 * nc + k] = kw * cos(th);
+        comp[3 * nc + k] = kw * sin(th);
+        comp[4 * nc + k] = dm->bnd.phase[k];
+        comp[5 * nc + k] = c * cos(th);
+        comp[6 * nc + k] = c * sin(th);
+    }
+    // initial state: h = max(d + eta0, 0), w = b + h
+    std::vector<T> w0((size_t)fs, (T)0), Pv((size_t)fs, (T)0), Qv((size_t)fs, (T)0);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = cidx(i, j), k = (size_t)i + (size_t)j * nx;
+            double h = fmax(dd[c] + (eta0 ? eta0[k] : 0.0), 0.0);
+            w0[c] = (T)(bC[c] + h);
+            Pv[c] = (T)(P0 ? P0[k] : 0.0);
+            Qv[c] = (T)(Q0 ? Q0[k] : 0.0);
+        }
+    std::vector<T> cornerT(corner.size()), bCT((size_t)fs);
+    for (size_t q = 0; q < corner.size(); q++) cornerT[q] = (T)corner[q];
+    for (size_t q = 0; q < (size_t)fs; q++) bCT[q] = (T)bC[q];
+
+    // ---- device memory: one allocation
+    const size_t fb = align256((size_t)fs * sizeof(T));
+    const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
+    const int nfields = nstate + 15 + 2 + 1 + 6;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    size_t o_fields = take(fb * nfields);
+    size_t o_corner = take(cornerT.size() * sizeof(T));
+    size_t o_gx = take(nx * sizeof(T)), o_gy = take(ny * sizeof(T));
+    size_t o_corr = take((size_t)(2 * nx + 2 * ny) * sizeof(T));
+    size_t o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
+    size_t o_comp = take(comp.size() * sizeof(double));
+    size_t o_ctl = take(sizeof(Ctl)), o_coef = take(sizeof(Coef));
+    dm->mass_blocks = 512;
+    size_t o_mass = take(dm->mass_blocks * sizeof(double));
+    dm->dbytes = off;
+    if (cudaMalloc(&dm->dmem, off) != cudaSuccess) { dm->dmem = nullptr; return BSQ_ERR_OOM; }
+    char *base = (char *)dm->dmem;
+    CK(cudaMemsetAsync(base, 0, off, dm->stream));
+    Dev<T> &D = dev_of<T>(dm);
+    memset(&D, 0, sizeof(D));
+    D.nx = nx; D.ny = ny; D.pitch = pitch; D.hx = hx; D.fstride = fstride;
+    D.dx = (T)p.dx; D.dy = (T)p.dy; D.rdx = (T)(1.0 / p.dx); D.rdy = (T)(1.0 / p.dy);
+    D.dxd = p.dx; D.dyd = p.dy;
+    D.g = (T)p.g; D.Bd = (T)p.Bd; D.w_s = (T)p.w_s; D.friction = (T)p.friction; D.theta = (T)p.theta;
+    double eps = p.eps > 0.0 ? p.eps : pow(fmax(p.dx, p.dy), 4);
+    D.eps = (T)eps;
+    D.kahan = kahan ? 1 : 0;
+    D.cross_mode = p.cross_mode;
+    for (int s = 0; s < 4; s++) D.bc[s] = bt[s];
+    D.cfl = p.cfl; D.ema_alpha = p.ema_alpha; D.dt_init = p.dt_init; D.dt_min = p.dt_min;
+    D.dt_max = p.dt_max; D.ramp_time = p.ramp_time;
+    T *F = (T *)(base + o_fields);
+    auto field = [&](int k) { return (T *)((char *)F + fb * k); };
+    int k = 0;
+    D.w[0] = field(k++); D.w[1] = field(k++); D.P = field(k++); D.Q = field(k++);
+    if (kahan) { D.cw = field(k++); D.cP = field(k++); D.cQ = field(k++); }
+    else { D.cw = D.cP = D.cQ = nullptr; }
+    D.hist = field(k); k += 15;
+    D.dU = field(k++); D.dV = field(k++);
+    D.bC = field(k++);
+    D.fxm = field(k++); D.fxe = field(k++); D.fxc = field(k++);
+    D.fym = field(k++); D.fye = field(k++); D.fyc = field(k++);
+    D.corner = (T *)(base + o_corner);
+    D.cpitch = cx;
+    D.gx = (T *)(base + o_gx);
+    D.gy = (T *)(base + o_gy);
+    T *corr = (T *)(base + o_corr);
+    D.corrW = corr; D.corrE = corr + ny; D.corrS = corr + 2 * ny; D.corrN = corr + 2 * ny + nx;
+    double *cb = (double *)(base + o_cb);
+    D.cW = cb; D.cE = cb + ny; D.cS = cb + 2 * ny; D.cN = cb + 2 * ny + nx;
+    double *cp = (double *)(base + o_comp);
+    D.ncomp = nc;
+    D.amp = cp; D.om = cp + nc; D.kx = cp + 2 * nc; D.ky = cp + 3 * nc; D.ph = cp + 4 * nc;
+    D.cx = cp + 5 * nc; D.cy = cp + 6 * nc;
+    D.ctl = (Ctl *)(base + o_ctl);
+    D.coef = (Coef *)(base + o_coef);
+    dm->ctl = D.ctl;
+    dm->coef = D.coef;
+    dm->mass_partial = (double *)(base + o_mass);
+    dm->n_state_fields = nstate + 15;
+
+    // uploads (synchronous copies from pageable memory, then a stream sync)
+    const size_t fbytes = (size_t)fs * sizeof(T);
+    CK(cudaStreamSynchronize(dm->stream));
+    CK(cudaMemcpy(D.w[0], w0.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.P, Pv.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.Q, Qv.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.bC, bCT.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fxm, fxm.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fxe, fxe.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fxc, fxc.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fym, fym.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fye, fye.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.fyc, fyc.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.corner, cornerT.data(), cornerT.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.gx, gx.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.gy, gy.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
+    std::vector<double> cbh;
+    cbh.insert(cbh.end(), cW.begin(), cW.end());
+    cbh.insert(cbh.end(), cE.begin(), cE.end());
+    cbh.insert(cbh.end(), cS.begin(), cS.end());
+    cbh.insert(cbh.end(), cN.begin(), cN.end());
+    CK(cudaMemcpy(cb, cbh.data(), cbh.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (nc > 0) CK(cudaMemcpy(cp, comp.data(), comp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    Ctl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.t_end = INFINITY;
+    c0.n_limit = 0x7fffffffffffffffLL;
+    CK(cudaMemcpy(D.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice));
+    CK(configure<T>(nx));
+    CK(launch_rate<T>(D, dm->stream, 0));
+    return wait_stream(dm, 600.0);
+}
+
+extern "C" bsq_status bsq_create(const bsq_params *p, const double *bed_corners, const bsq_boundary *bnd,
+                                 const double *eta0, const double *P0, const double *Q0, void *cuda_stream,
+                                 bsq_domain **out)
+{
+    if (!out) return BSQ_ERR_ARG;
+    *out = nullptr;
+    if (!p || !bed_corners) return BSQ_ERR_ARG;
+    if (p->nx < 3 || p->ny < 3 || p->nx > 16384 || p->ny > 16384) return BSQ_ERR_ARG;
+    if (!(p->dx > 0) || !(p->dy > 0) || !(p->g > 0) || !(p->cfl > 0) || !(p->ema_alpha > 0) ||
+        p->ema_alpha > 1.0 || p->Bd < 0 || (p->precision != BSQ_FP32 && p->precision != BSQ_FP64) ||
+        (p->cross_mode != 0 && p->cross_mode != 1))
+        return BSQ_ERR_ARG;
+    bsq_boundary b;
+    memset(&b, 0, sizeof(b));
+    if (bnd) {
+        b = *bnd;
+        for (int s = 0; s < 4; s++)
+            if (b.type[s] < 0 || b.type[s] > 2) return BSQ_ERR_ARG;
+        bool maker = false;
+        for (int s = 0; s < 4; s++) maker |= b.type[s] == BSQ_BC_MAKER;
+        if (maker && (b.n_comp <= 0 || !b.amp || !b.freq || !b.phase || !b.dir)) return BSQ_ERR_ARG;
+        if (b.n_comp < 0) return BSQ_ERR_ARG;
+    }
+    bsq_domain *d = new (std::nothrow) bsq_domain;
+    if (!d) return BSQ_ERR_OOM;
+    memset((void *)d, 0, sizeof(*d));
+    d->p = *p;
+    if (d->p.timeout_s <= 0) d->p.timeout_s = 600.0;
+    d->graph_steps = p->graph_steps > 0 ? p->graph_steps : 16;
+    d->bnd = b;
+    // copy the component arrays (the caller's pointers are not kept)
+    std::vector<double> comps;
+    if (b.n_comp > 0 && b.amp) {
+        comps.resize((size_t)4 * b.n_comp);
+        memcpy(&comps[0], b.amp, b.n_comp * sizeof(double));
+        memcpy(&comps[b.n_comp], b.freq, b.n_comp * sizeof(double));
+        memcpy(&comps[2 * b.n_comp], b.phase, b.n_comp * sizeof(double));
+        memcpy(&comps[3 * b.n_comp], b.dir, b.n_comp * sizeof(double));
+        d->bnd.amp = &comps[0];
+        d->bnd.freq = &comps[b.n_comp];
+        d->bnd.phase = &comps[2 * b.n_comp];
+        d->bnd.dir = &comps[3 * b.n_comp];
+    }
+    d->fp64 = p->precision == BSQ_FP64;
+    d->nx = p->nx;
+    d->ny = p->ny;
+    if (cuda_stream) {
+        d->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete d;
+            return BSQ_ERR_CUDA;
+        }
+        d->own_stream = 1;
+    }
+    if (cudaMallocHost((void **)&d->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+        d->h_ctl = nullptr;
+        bsq_destroy(d);
+        return BSQ_ERR_OOM;
+    }
+    bsq_status st = d->fp64 ? create_T<double>(d, bed_corners, eta0, P0, Q0)
+                            : create_T<float>(d, bed_corners, eta0, P0, Q0);
+    d->bnd.amp = d->bnd.freq = d->bnd.phase = d->bnd.dir = nullptr;
+    if (st != BSQ_OK) {
+        bsq_destroy(d);
+        return st;
+    }
+    *out = d;
+    return BSQ_OK;
+}
+
+extern "C" void bsq_destroy(bsq_domain *d)
+{
+    if (!d) return;
+    if (d->stream) cudaStreamSynchronize(d->stream);
+    if (d->graph) cudaGraphExecDestroy(d->graph);
+    if (d->dmem) cudaFree(d->dmem);
+    if (d->h_ctl) cudaFreeHost(d->h_ctl);
+    if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
+    delete d;
+}
+
+extern "C" size_t bsq_device_bytes(const bsq_domain *d) { return d ? d->dbytes : 0; }
+
+// ------------------------------------------------------------------ stepping
+
+static cudaError_t enqueue_step(bsq_domain *d, double forced_dt)
+{
+    return d->fp64 ? launch_step<double>(d->Dd, d->stream, forced_dt)
+                   : launch_step<float>(d->Df, d->stream, forced_dt);
+}
+
+static bsq_status read_ctl(const bsq_domain *d)
+{
+    CK(cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, d->stream));
+    return wait_stream(d);
+}
+
+static bsq_status ctl_status(const Ctl &c)
+{
+    if (c.err & ERR_NONFINITE) return BSQ_ERR_NONFINITE;
+    if (c.err & (ERR_UNSTABLE | ERR_NODT)) return BSQ_ERR_UNSTABLE;
+    return BSQ_OK;
+}
+
+static bsq_status build_graph(bsq_domain *d)
+{
+    if (d->graph) return BSQ_OK;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < d->graph_steps && e == cudaSuccess; s++) e = enqueue_step(d, 0.0);
+    cudaError_t e2 = cudaStreamEndCapture(d->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) return BSQ_ERR_CUDA;
+    e = cudaGraphInstantiate(&d->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { d->graph = nullptr; return BSQ_ERR_CUDA; }
+    return BSQ_OK;
+}
+
+extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done)
+{
+    if (steps_done) *steps_done = 0;
+    if (!d) return BSQ_ERR_ARG;
+    if (d->sticky != BSQ_OK) return d->sticky;
+    if (isnan(t_end)) return BSQ_ERR_ARG;
+    bsq_status st = read_ctl(d);
+    if (st != BSQ_OK) return set_sticky(d, st);
+    const long long n0 = d->h_ctl->n;
+    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, t_end, max_steps)) return set_sticky(d, BSQ_ERR_CUDA);
+    st = build_graph(d);
+    if (st != BSQ_OK) return set_sticky(d, st);
+    if (max_steps > 0) {
+        long long ng = (max_steps + d->graph_steps - 1) / d->graph_steps;
+        const long long chunk = 64;
+        for (long long q = 0; q < ng; q += chunk) {
+            long long m = ng - q < chunk ? ng - q : chunk;
+            for (long long r = 0; r < m; r++)
+                if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+            st = read_ctl(d);
+            if (st != BSQ_OK) return set_sticky(d, st);
+            st = ctl_status(*d->h_ctl);
+            if (st != BSQ_OK) break;
+            double tol = 1e-12 * fmax(1.0, fabs(t_end));
+            if (!(d->h_ctl->t < t_end - tol)) break;
+        }
+    } else {
+        int batch = 1;
+        for (;;) {
+            for (int r = 0; r < batch; r++)
+                if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+            st = read_ctl(d);
+            if (st != BSQ_OK) return set_sticky(d, st);
+            st = ctl_status(*d->h_ctl);
+            if (st != BSQ_OK) break;
+            double tol = 1e-12 * fmax(1.0, fabs(t_end));
+            if (!(d->h_ctl->t < t_end - tol)) break;
+            if (batch < 64) batch *= 2;
+        }
+    }
+    if (steps_done) *steps_done = d->h_ctl->n - n0;
+    return set_sticky(d, st);
+}
+
+extern "C" bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n)
+{
+    if (!d || (n > 0 && !dts) || n < 0) return BSQ_ERR_ARG;
+    if (d->sticky != BSQ_OK) return d->sticky;
+    for (long long q = 0; q < n; q++)
+        if (!(dts[q] > 0.0) || !isfinite(dts[q])) return BSQ_ERR_ARG;
+    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, INFINITY, 0)) return set_sticky(d, BSQ_ERR_CUDA);
+    for (long long q = 0; q < n; q++) {
+        if (enqueue_step(d, dts[q]) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+        if ((q & 255) == 255) {
+            bsq_status st = read_ctl(d);
+            if (st != BSQ_OK) return set_sticky(d, st);
+            st = ctl_status(*d->h_ctl);
+            if (st != BSQ_OK) return set_sticky(d, st);
+        }
+    }
+    bsq_status st = read_ctl(d);
+    if (st != BSQ_OK) return set_sticky(d, st);
+    return set_sticky(d, ctl_status(*d->h_ctl));
+}
+
+// ------------------------------------------------------------------ outputs
+
+extern "C" bsq_status bsq_read_device(const bsq_domain *d, int field, void *dev_out)
+{
+    if (!d || !dev_out || field < 0 || field > 4) return BSQ_ERR_ARG;
+    if (d->sticky != BSQ_OK && d->sticky != BSQ_ERR_NONFINITE && d->sticky != BSQ_ERR_UNSTABLE)
+        return d->sticky;
+    bsq_status st = read_ctl(d);
+    if (st != BSQ_OK) return st;
+    int wc = (int)(d->h_ctl->n & 1);
+    cudaError_t e = d->fp64 ? launch_extract<double>(d->Dd, d->stream, wc, field, (double *)dev_out)
+                            : launch_extract<float>(d->Df, d->stream, wc, field, (float *)dev_out);
+    return e == cudaSuccess ? BSQ_OK : BSQ_ERR_CUDA;
+}
+
+extern "C" bsq_status bsq_read(const bsq_domain *d, int field, double *host_out)
+{
+    if (!d || !host_out || field < 0 || field > 4) return BSQ_ERR_ARG;
+    size_t ncell = (size_t)d->nx * d->ny;
+    size_t esz = d->fp64 ? 8 : 4;
+    void *tmp = nullptr;
+    if (cudaMallocAsync(&tmp, ncell * esz, d->stream) != cudaSuccess) return BSQ_ERR_OOM;
+    bsq_status st = bsq_read_device(d, field, tmp);
+    std::vector<float> hf;
+    if (st == BSQ_OK) {
+        if (d->fp64) {
+            if (cudaMemcpyAsync(host_out, tmp, ncell * 8, cudaMemcpyDeviceToHost, d->stream) != cudaSuccess)
+                st = BSQ_ERR_CUDA;
+        } else {
+            hf.resize(ncell);
+            if (cudaMemcpyAsync(hf.data(), tmp, ncell * 4, cudaMemcpyDeviceToHost, d->stream) != cudaSuccess)
+                st = BSQ_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(tmp, d->stream);
+    bsq_status w = wait_stream(d);
+    if (st == BSQ_OK) st = w;
+    if (st == BSQ_OK && !d->fp64)
+        for (size_t q = 0; q < ncell; q++) host_out[q] = (double)hf[q];
+    return st;
+}
+
+extern "C" bsq_status bsq_info(const bsq_domain *d, double *t, long long *n, double *last_dt, double *mass,
+                               long long *clamps)
+{
+    if (!d) return BSQ_ERR_ARG;
+    bsq_status st = read_ctl(d);
+    if (st != BSQ_OK) return st;
+    Ctl c = *d->h_ctl;
+    if (t) *t = c.t;
+    if (n) *n = c.n;
+    if (last_dt) *last_dt = c.last_dt;
+    if (clamps) *clamps = (long long)c.clamps;
+    if (mass) {
+        int wc = (int)(c.n & 1);
+        cudaError_t e = d->fp64 ? launch_mass<double>(d->Dd, d->stream, wc, d->mass_partial, d->mass_blocks)
+                                : launch_mass<float>(d->Df, d->stream, wc, d->mass_partial, d->mass_blocks);
+        if (e != cudaSuccess) return BSQ_ERR_CUDA;
+        std::vector<double> part(d->mass_blocks);
+        CK(cudaMemcpyAsync(part.data(), d->mass_partial, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           d->stream));
+        st = wait_stream(d);
+        if (st != BSQ_OK) return st;
+        double s = 0.0;
+        for (double v : part) s += v;
+        *mass = s * d->p.dx * d->p.dy;
+    }
+    return ctl_status(c) == BSQ_OK ? d->sticky : ctl_status(c);
+}
+
+// ------------------------------------------------------------------ checkpoint
+
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, precision, kahan, cross_mode, nfields, pad;
+    long long fstride;
+};
+
+static void state_ptrs(const bsq_domain *d, std::vector<void *> &ptrs, size_t &fbytes)
+{
+    if (d->fp64) {
+        const Dev<double> &D = d->Dd;
+        ptrs = {D.w[0], D.w[1], D.P, D.Q};
+        for (int k = 0; k < 15; k++) ptrs.push_back(D.hist + (size_t)k * D.fstride);
+        fbytes = (size_t)D.fstride * 8;
+    } else {
+        const Dev<float> &D = d->Df;
+        ptrs = {D.w[0], D.w[1], D.P, D.Q};
+        if (D.kahan) { ptrs.push_back(D.cw); ptrs.push_back(D.cP); ptrs.push_back(D.cQ); }
+        for (int k = 0; k < 15; k++) ptrs.push_back(D.hist + (size_t)k * D.fstride);
+        fbytes = (size_t)D.fstride * 4;
+    }
+}
+
+extern "C" bsq_status bsq_checkpoint(const bsq_domain *d, void *buf, size_t *len)
+{
+    if (!d || !len) return BSQ_ERR_ARG;
+    std::vector<void *> ptrs;
+    size_t fbytes;
+    state_ptrs(d, ptrs, fbytes);
+    size_t need = sizeof(CkptHeader) + sizeof(Ctl) + ptrs.size() * fbytes;
+    if (!buf) { *len = need; return BSQ_OK; }
+    if (*len < need) { *len = need; return BSQ_ERR_ARG; }
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "BSQCKPT", 8);
+    h.version = 1; h.nx = d->nx; h.ny = d->ny; h.precision = d->fp64; h.kahan = d->p.kahan;
+    h.cross_mode = d->p.cross_mode; h.nfields = (int)ptrs.size(); h.fstride = d->fstride;
+    char *o = (char *)buf;
+    memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    CK(cudaMemcpyAsync(o, d->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, d->stream));
+    o += sizeof(Ctl);
+    for (void *p : ptrs) {
+        CK(cudaMemcpyAsync(o, p, fbytes, cudaMemcpyDeviceToHost, d->stream));
+        o += fbytes;
+    }
+    *len = need;
+    return wait_stream(d);
+}
+
+extern "C" bsq_status bsq_restore(bsq_domain *d, const void *buf, size_t len)
+{
+    if (!d || !buf) return BSQ_ERR_ARG;
+    std::vector<void *> ptrs;
+    size_t fbytes;
+    state_ptrs(d, ptrs, fbytes);
+    size_t need = sizeof(CkptHeader) + sizeof(Ctl) + ptrs.size() * fbytes;
+    if (len < need) return BSQ_ERR_ARG;
+    CkptHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, "BSQCKPT", 8) != 0 || h.version != 1 || h.nx != d->nx || h.ny != d->ny ||
+        h.precision != d->fp64 || h.kahan != d->p.kahan || h.nfields != (int)ptrs.size() ||
+        h.fstride != d->fstride)
+        return BSQ_ERR_ARG;
+    const char *o = (const char *)buf + sizeof(h);
+    bsq_status st = wait_stream(d);
+    if (st != BSQ_OK) return st;
+    CK(cudaMemcpy(d->ctl, o, sizeof(Ctl), cudaMemcpyHostToDevice));
+    o += sizeof(Ctl);
+    for (void *p : ptrs) {
+        CK(cudaMemcpy(p, o, fbytes, cudaMemcpyHostToDevice));
+        o += fbytes;
+    }
+    d->sticky = BSQ_OK;
+    return BSQ_OK;
+}
+
+// ------------------------------------------------------------------ profiling
+
+static const char *kKernelNames[] = {"ctl_ghost", "rhs_combine", "ysolve", "ghost_q", "xsolve"};
+
+extern "C" const char *bsq_kernel_name(int k)
+{
+    return (k >= 0 && k < 5) ? kKernelNames[k] : "";
+}
+
+extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels)
+{
+    if (!d || !ms_out || !n_kernels || n_steps <= 0) return BSQ_ERR_ARG;
+    if (d->sticky != BSQ_OK) return d->sticky;
+    cudaEvent_t ev[6];
+    for (int k = 0; k < 6; k++)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) return BSQ_ERR_CUDA;
+    for (int k = 0; k < 5; k++) ms_out[k] = 0.0;
+    bsq_status st = BSQ_OK;
+    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, INFINITY, n_steps)) st = BSQ_ERR_CUDA;
+    for (long long q = 0; q < n_steps && st == BSQ_OK; q++) {
+        cudaError_t e = d->fp64 ? launch_step_timed<double>(d->Dd, d->stream, 0.0, ev)
+                                : launch_step_timed<float>(d->Df, d->stream, 0.0, ev);
+        if (e != cudaSuccess) { st = BSQ_ERR_CUDA; break; }
+        st = wait_stream(d);
+        if (st != BSQ_OK) break;
+        for (int k = 0; k < 5; k++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) { st = BSQ_ERR_CUDA; break; }
+            ms_out[k] += ms;
+        }
+    }
+    for (int k = 0; k < 6; k++) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 5; k++) ms_out[k] /= (double)n_steps;
+    *n_kernels = 5;
+    if (st == BSQ_OK) {
+        st = read_ctl(d);
+        if (st == BSQ_OK) st = ctl_status(*d->h_ctl);
+    }
+    return set_sticky(d, st);
+}

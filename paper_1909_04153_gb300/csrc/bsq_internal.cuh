@@ -1,0 +1,90 @@
+// bsq_internal.cuh -- device-side data structures and helpers of the GB300
+// extended Boussinesq solver (arXiv 1909.04153).  Shared by the kernels and
+// the host engine of the library; nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bsq {
+
+enum { WALL = 0, SPONGE = 1, MAKER = 2 };
+enum { SW = 0, SE = 1, SS = 2, SN = 3 };
+
+// error flags raised on the device
+enum : unsigned { ERR_NONFINITE = 1u, ERR_UNSTABLE = 2u, ERR_NODT = 4u };
+
+// Controller state of one domain (FP64, device resident).  The controller
+// kernel reads it; the first block of the stencil kernel commits the step.
+struct Ctl {
+    double t;                 // simulated time of level n
+    double dtm1, dtm2;        // dt_{n-1}, dt_{n-2}
+    double t_end;             // advance target
+    double last_dt;
+    long long n;              // steps taken
+    long long n_limit;        // no step starts once n >= n_limit
+    unsigned long long rate_bits;  // Eq. 22 rate of the current state (bits of a positive double)
+    unsigned long long clamps;     // positivity clamps so far
+    unsigned int err;
+    int pad;
+};
+
+// Per-step coefficients written by the controller, read by the step kernels.
+struct Coef {
+    int active;               // 1: this step does work
+    int s0, s1, s2;           // ring slots of levels n, n-1, n-2
+    int nlev;                 // history levels used (1: first Euler step, 2, 3)
+    int wc;                   // index of the w buffer holding level n
+    long long n;
+    double t0, t1, dt;
+    double beta[3], gam[3];
+    float betaf[3], gamf[3];
+};
+
+// Everything a kernel needs, passed by value.  T = float or double.
+template <typename T>
+struct Dev {
+    int nx, ny;
+    int pitch;                // elements per padded row
+    int hx;                   // halo columns left of the interior
+    long long fstride;        // elements per padded field
+    T dx, dy, rdx, rdy;       // cell sizes and reciprocals
+    double dxd, dyd;          // cell sizes in FP64 (wave-maker phases)
+    T g, Bd, eps, w_s, friction, theta;
+    int kahan, cross_mode;
+    int bc[4];
+    // controller inputs (FP64)
+    double cfl, ema_alpha, dt_init, dt_min, dt_max;
+    double ramp_time;
+    // state (padded fields with a 2-cell halo)
+    T *w[2];                  // ping-pong water level
+    T *cw, *P, *cP, *Q, *cQ;  // fluxes and compensation terms
+    T *hist;                  // 5 fields x 3 levels, field f slot s at hist + (3 f + s) fstride
+    T *dU, *dV;               // increments for the line solves (scratch)
+    // static fields
+    T *corner;                // bed at corners, (nx+5) x (ny+5), origin (-2,-2)
+    int cpitch;
+    T *bC;                    // bed at cell centres (padded field, halo included)
+    T *fxm, *fxe, *fxc;       // x-line Thomas factors: m, -a m, c m
+    T *fym, *fye, *fyc;       // y-line Thomas factors
+    T *gx, *gy;               // sponge factor profiles along x and y (product of sides)
+    const double *cW, *cE, *cS, *cN;  // raw boundary coefficients for maker rows
+    T *corrW, *corrE, *corrS, *corrN; // per-step maker corrections of the line right-hand sides
+    // wave maker
+    int ncomp;
+    const double *amp, *om, *kx, *ky, *ph, *cx, *cy;
+    // controller
+    Ctl *ctl;
+    Coef *coef;
+};
+
+template <typename T>
+__host__ __device__ inline long long fidx(const Dev<T> &D, int i, int j)
+{
+    return (long long)(j + 2) * D.pitch + (i + D.hx);
+}
+
+__device__ inline unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ inline double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+}  // namespace bsq

@@ -1,0 +1,23 @@
+// bsq_launch.h -- launchers of the step kernels (bsq_kernels.cu), called by
+// the host engine (bsq_host.cu).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "bsq_internal.cuh"
+
+namespace bsq {
+
+template <typename T> int step_shape_ok(int nx, int ny);
+template <typename T> size_t xsolve_smem(int nx);
+template <typename T> int row_segment();
+template <typename T> cudaError_t configure(int nx);
+template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, double forced_dt);
+template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
+template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, int wc);
+template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
+template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);
+cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long max_steps);
+
+}  // namespace bsq

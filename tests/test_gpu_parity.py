@@ -1,0 +1,221 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+With the oracle's dt sequence replayed (bsq_step_dt):
+  * FP64 GPU within 1e-10 relative L2 of the oracle in eta, P and Q;
+  * FP32 with compensated accumulation within 1e-4 relative L2 in eta after
+    1000 steps.
+Adaptive runs compare the dt traces.  Sizes span several stencil tiles,
+several x-line segments and y-line chunks, and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_04153_gb300 import bsq
+from paper_1909_04153_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _oracle(case, **over):
+    p = dict(case["params"])
+    p.update(over)
+    return oracle.OracleDomain(p, case["bed"], case["comps"], case["eta0"], case["P0"], case["Q0"])
+
+
+def _smooth_bed(nx, ny, dx, seed=3, lo=0.3, hi=1.1):
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.arange(nx + 1) * dx, np.arange(ny + 1) * dx)
+    b = np.zeros_like(X)
+    for _ in range(4):
+        kx, ky, ph = rng.uniform(0.1, 0.6), rng.uniform(0.1, 0.6), rng.uniform(0, 6.28)
+        b += np.cos(kx * X + ph) * np.cos(ky * Y)
+    b = (b - b.min()) / (b.max() - b.min())
+    return -(lo + (hi - lo) * b)
+
+
+def _hump_case(nx, ny, dx=0.1, seed=3):
+    bed = _smooth_bed(nx, ny, dx, seed)
+    xc, yc = (np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(xc, yc)
+    eta = 0.06 * np.exp(-((X - 0.3 * nx * dx) ** 2 + (Y - 0.4 * ny * dx) ** 2) / (0.02 * (nx * dx) ** 2))
+    return dict(params=W.base_params(nx, ny, dx, cfl=0.125), bed=bed, comps=None, eta0=eta, P0=None, Q0=None)
+
+
+CASES = {
+    "hump_2d_walls": lambda: _hump_case(77, 45),
+    "barred_beach_rips": lambda: W.barred_beach(nx=96, ny=72),
+    "planar_beach_jonswap": lambda: W.planar_beach(nx=160, ny=20),
+    "solitary_channel": lambda: W.solitary_basin(nx=129, ny=9, dx=0.1),
+    "ragged_multi_segment": lambda: _hump_case(301, 37, dx=0.05, seed=5),
+    "tall_multi_chunk": lambda: _hump_case(35, 530, dx=0.05, seed=7),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_replay_matches_oracle(name):
+    case = CASES[name]()
+    steps = 150
+    o = _oracle(case)
+    dts = o.run(steps)
+    with bsq.Domain(case, precision="fp64") as d:
+        d.step_dt(dts)
+        info = d.info()
+        assert info["n"] == steps
+        assert abs(info["t"] - o.info()["t"]) <= 1e-12 * o.info()["t"]
+        for f in ("eta", "P", "Q"):
+            ref, got = o.get(f), d.read(f)
+            if np.linalg.norm(ref) == 0.0:
+                assert np.abs(got).max() <= 1e-13, f
+            else:
+                assert rel(got, ref) <= FP64_TOL, (f, rel(got, ref))
+        assert info["clamps"] == o.info()["clamps"]
+
+
+def test_fp64_extrapolated_cross_terms_match_oracle():
+    # cross_mode 0 (both F*, G* extrapolated as in Eqs. 17-18 / 43) on a grid
+    # where that form is stable (d/dx <= 1.1)
+    case = _hump_case(64, 48, dx=1.0, seed=11)
+    o = _oracle(case, cross_mode=0)
+    dts = o.run(200)
+    with bsq.Domain(case, precision="fp64", cross_mode=0) as d:
+        d.step_dt(dts)
+        for f in ("eta", "P", "Q"):
+            assert rel(d.read(f), o.get(f)) <= FP64_TOL, f
+
+
+def test_fp64_adaptive_dt_trace_matches_oracle():
+    case = W.barred_beach(nx=80, ny=64)
+    o = _oracle(case)
+    ref = [o.step() or o.info()["last_dt"] for _ in range(120)]
+    with bsq.Domain(case, precision="fp64", graph_steps=7) as d:
+        got = []
+        for _ in range(120):
+            d.advance(max_steps=1)
+            got.append(d.info()["last_dt"])
+    np.testing.assert_allclose(got, ref, rtol=1e-8)
+
+
+def test_fp64_advance_lands_on_t_end_like_oracle():
+    case = W.solitary_basin(nx=64, ny=12)
+    o = _oracle(case)
+    tr = o.advance(0.37)
+    with bsq.Domain(case, precision="fp64", graph_steps=5) as d:
+        n = d.advance(0.37)
+        info = d.info()
+    assert n == len(tr)
+    assert abs(info["t"] - 0.37) <= 1e-14
+    assert abs(info["last_dt"] - tr[-1]) <= 1e-8 * tr[-1]
+
+
+@pytest.mark.parametrize("name", ["barred_beach_rips", "hump_2d_walls"])
+def test_fp32_kahan_1000_steps_matches_oracle(name):
+    case = CASES[name]()
+    o = _oracle(case)
+    dts = o.run(1000)
+    with bsq.Domain(case, precision="fp32", kahan=True) as d:
+        d.step_dt(dts)
+        e = rel(d.read("eta"), o.get("eta"))
+        assert e <= FP32_TOL, e
+        # fluxes reported, looser (the oracle itself only pins eta here)
+        assert rel(d.read("P"), o.get("P")) <= 1e-3
+        assert rel(d.read("Q"), o.get("Q")) <= 1e-3
+
+
+def test_fp32_without_kahan_runs():
+    case = CASES["hump_2d_walls"]()
+    o = _oracle(case)
+    dts = o.run(300)
+    with bsq.Domain(case, precision="fp32", kahan=False) as d:
+        d.step_dt(dts)
+        assert rel(d.read("eta"), o.get("eta")) <= 1e-3
+
+
+# ------------------------------------------------------------------ invariants
+
+def test_gpu_lake_at_rest_fp64_and_fp32():
+    nx, ny, dx = 70, 50, 0.1
+    case = dict(params=W.base_params(nx, ny, dx, cfl=0.125), bed=_smooth_bed(nx, ny, dx), comps=None,
+                eta0=None, P0=None, Q0=None)
+    with bsq.Domain(case, precision="fp64") as d:
+        d.advance(max_steps=1000)
+        assert np.abs(d.read("eta")).max() <= 1e-13
+        assert np.abs(d.read("P")).max() <= 1e-13 and np.abs(d.read("Q")).max() <= 1e-13
+    with bsq.Domain(case, precision="fp32") as d:
+        d.advance(max_steps=1000)
+        assert np.abs(d.read("eta")).max() <= 1e-5
+        assert np.abs(d.read("P")).max() <= 1e-5
+
+
+def test_gpu_mass_conservation_fp64():
+    case = _hump_case(90, 66, seed=9)
+    with bsq.Domain(case, precision="fp64") as d:
+        m0 = d.info()["mass"]
+        d.advance(max_steps=500)
+        info = d.info()
+        assert info["clamps"] == 0
+        assert abs(info["mass"] - m0) <= 1e-12 * m0
+
+
+def test_tiny_grid_3x3():
+    case = _hump_case(3, 3, dx=0.2)
+    o = _oracle(case)
+    dts = o.run(30)
+    with bsq.Domain(case, precision="fp64") as d:
+        d.step_dt(dts)
+        for f in ("eta", "P", "Q"):
+            ref = o.get(f)
+            got = d.read(f)
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), f
+
+
+def test_checkpoint_restore_is_bitwise():
+    case = W.barred_beach(nx=72, ny=40)
+    for prec in ("fp32", "fp64"):
+        with bsq.Domain(case, precision=prec) as a, bsq.Domain(case, precision=prec) as b:
+            a.advance(max_steps=50)
+            snap = a.checkpoint()
+            a.advance(max_steps=60)
+            b.restore(snap)
+            b.advance(max_steps=60)
+            for f in ("eta", "P", "Q"):
+                np.testing.assert_array_equal(a.read(f), b.read(f))
+            assert a.info()["t"] == b.info()["t"]
+
+
+# ------------------------------------------------------------------ failure detection (host-made)
+
+def test_nonfinite_input_is_reported():
+    case = _hump_case(40, 30)
+    P0 = np.zeros((30, 40))
+    P0[10, 12] = np.nan
+    case["P0"] = P0
+    with bsq.Domain(case, precision="fp32") as d:
+        with pytest.raises(bsq.BsqError) as ei:
+            d.advance(max_steps=5)
+        assert ei.value.status == bsq.ERR_NONFINITE
+        with pytest.raises(bsq.BsqError):  # sticky
+            d.advance(max_steps=1)
+
+
+def test_dt_below_dt_min_is_unstable():
+    case = _hump_case(40, 30)
+    with bsq.Domain(case, precision="fp64", dt_min=1.0) as d:
+        with pytest.raises(bsq.BsqError) as ei:
+            d.advance(max_steps=3)
+        assert ei.value.status == bsq.ERR_UNSTABLE
+
+
+def test_bounded_wait_times_out():
+    case = W.barred_beach(nx=512, ny=512)
+    with bsq.Domain(case, precision="fp64", timeout_s=1e-6) as d:
+        with pytest.raises(bsq.BsqError) as ei:
+            d.advance(max_steps=2000)
+        assert ei.value.status == bsq.ERR_TIMEOUT
