@@ -516,7 +516,7 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
     if (steps_done) *steps_done = 0;
     if (!d) return BSQ_ERR_ARG;
     if (d->sticky != BSQ_OK) return d->sticky;
-    if (isnan(t_end)) return BSQ_ERR_ARG;
+    if (isnan(t_end) || (max_steps <= 0 && !isfinite(t_end))) return BSQ_ERR_ARG;
     bsq_status st = read_ctl(d);
     if (st != BSQ_OK) return set_sticky(d, st);
     const long long n0 = d->h_ctl->n;
@@ -534,7 +534,7 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
             if (st != BSQ_OK) return set_sticky(d, st);
             st = ctl_status(*d->h_ctl);
             if (st != BSQ_OK) break;
-            double tol = 1e-12 * fmax(1.0, fabs(t_end));
+            double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
             if (!(d->h_ctl->t < t_end - tol)) break;
         }
     } else {
@@ -546,7 +546,7 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
             if (st != BSQ_OK) return set_sticky(d, st);
             st = ctl_status(*d->h_ctl);
             if (st != BSQ_OK) break;
-            double tol = 1e-12 * fmax(1.0, fabs(t_end));
+            double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
             if (!(d->h_ctl->t < t_end - tol)) break;
             if (batch < 64) batch *= 2;
         }

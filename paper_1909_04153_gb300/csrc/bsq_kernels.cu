@@ -111,7 +111,7 @@ __device__ void controller(const Dev<T> &D, double forced_dt, Coef &cf, unsigned
     cf.wc = (int)(n & 1);
     cf.nlev = n == 0 ? 1 : (n == 1 ? 2 : 3);
     for (int k = 0; k < 3; k++) { cf.beta[k] = 0.0; cf.gam[k] = 0.0; cf.betaf[k] = 0.f; cf.gamf[k] = 0.f; }
-    double tol = 1e-12 * fmax(1.0, fabs(t_end));
+    double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
     if (cerr != 0u || n >= n_limit || !(t < t_end - tol)) return;
     double dt;
     if (forced_dt > 0.0) {
