@@ -168,6 +168,31 @@ size_t bsq_device_bytes(const bsq_domain *d);
 bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels);
 const char *bsq_kernel_name(int k);
 
+/* Allocation-free variant of the volume reduction that bsq_info's mass uses.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc, such as an application that owns every byte of device memory
+ * through its own pool or budget, or code whose stream another component may
+ * be capturing into a CUDA graph, where a device allocation would fail or
+ * disturb that owner.  It computes sum over cells of max(w - b, 0) * dx * dy
+ * for caller-owned device arrays w and b (precision BSQ_FP32 or BSQ_FP64,
+ * ny rows of nx values, rows pitch elements apart) and writes the double to
+ * the caller's device pointer mass_dev, enqueued on cuda_stream (NULL = the
+ * default stream); it does not wait for the result.
+ *   - Scratch: the per-row partial sums live in a fixed file-scope device
+ *     array of BSQ_NOALLOC_MAX_ROWS doubles (128 KiB), held on every device
+ *     that loads the library until the process exits.  ny above that limit
+ *     returns BSQ_ERR_ARG without touching the device.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     with that device current; make that first call before any stream
+ *     capture begins.
+ *   - All calls share the one array, and each call overwrites it, so calls
+ *     that overlap on the GPU (different streams, or threads) race: order them.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: BSQ_ERR_ARG (NULL pointer, bad sizes, ny too large), BSQ_ERR_CUDA. */
+#define BSQ_NOALLOC_MAX_ROWS 16384
+bsq_status bsq_mass_noalloc(int precision, const void *w_dev, const void *b_dev, int nx, int ny,
+                            long long pitch, double dx, double dy, double *mass_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,9 @@ def lib():
         L.bsq_profile_kernels.argtypes = [vp, ctypes.c_longlong, _DP, ctypes.POINTER(ctypes.c_int)]
         L.bsq_kernel_name.restype = ctypes.c_char_p
         L.bsq_kernel_name.argtypes = [ctypes.c_int]
+        L.bsq_mass_noalloc.restype = ctypes.c_int
+        L.bsq_mass_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                       ctypes.c_double, ctypes.c_double, vp, vp]
         _lib = L
     return _lib
 
@@ -204,6 +207,20 @@ def bsq_profile_kernels(h, n_steps: int) -> dict:
 
 def bsq_kernel_name(k: int) -> str:
     return lib().bsq_kernel_name(int(k)).decode()
+
+
+NOALLOC_MAX_ROWS = 16384
+
+
+def bsq_mass_noalloc(precision: int, w_dev: int, b_dev: int, nx: int, ny: int, pitch: int, dx: float, dy: float,
+                     mass_dev: int, stream: int | None = None) -> None:
+    """Volume of caller-owned device arrays into a caller-owned device double;
+    allocates nothing (scratch is a fixed static device array)."""
+    st = lib().bsq_mass_noalloc(int(precision), ctypes.c_void_p(w_dev), ctypes.c_void_p(b_dev), int(nx), int(ny),
+                                int(pitch), float(dx), float(dy), ctypes.c_void_p(mass_dev),
+                                ctypes.c_void_p(stream or 0))
+    if st != OK:
+        raise BsqError(st, "bsq_mass_noalloc")
 
 
 # ---------------------------------------------------------------- wrapper

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libbsq.so")
-SOURCES = ["bsq_kernels.cu", "bsq_host.cu"]
+SOURCES = ["bsq_kernels.cu", "bsq_host.cu", "bsq_noalloc.cu"]
 HEADERS = ["bsq_internal.cuh", "bsq_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
