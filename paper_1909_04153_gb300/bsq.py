@@ -30,7 +30,7 @@ class bsq_params(ctypes.Structure):
         ("friction", ctypes.c_double), ("theta", ctypes.c_double), ("eps", ctypes.c_double),
         ("w_s", ctypes.c_double), ("ramp_time", ctypes.c_double), ("timeout_s", ctypes.c_double),
         ("precision", ctypes.c_int), ("kahan", ctypes.c_int), ("cross_mode", ctypes.c_int),
-        ("graph_steps", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("tune", ctypes.c_int * 4),
     ]
 
 
@@ -250,6 +250,8 @@ class Domain:
         p.cross_mode = int(prm.get("cross_mode", 1))
         if "graph_steps" in prm:
             p.graph_steps = int(prm["graph_steps"])
+        for q, v in enumerate(prm.get("tune", ()) or ()):
+            p.tune[q] = int(v)
         b = bsq_boundary()
         bc = prm.get("bc", (WALL, WALL, WALL, WALL))
         sw = prm.get("sponge_width", (0.0, 0.0, 0.0, 0.0))

@@ -18,6 +18,10 @@ LIB = os.path.join(OUT, "libbsq.so")
 SOURCES = ["bsq_kernels.cu", "bsq_host.cu", "bsq_noalloc.cu"]
 HEADERS = ["bsq_internal.cuh", "bsq_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The step kernels compile single-precision sqrt, division and reciprocal to
+# the approximate hardware forms (double precision is not affected).
+FAST_MATH = ["-use_fast_math"]
+FAST_MATH_SOURCES = ["bsq_kernels.cu"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
 
@@ -44,7 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
 
     def compile_one(src, obj):
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        extra = FAST_MATH if src in FAST_MATH_SOURCES else []
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -145,8 +145,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     const bsq_params &p = dm->p;
     const int nx = p.nx, ny = p.ny;
     const int hx = 16 / (int)sizeof(T);
-    const int seg = row_segment<T>();
-    const int pitch = ((nx + seg - 1) / seg) * seg + seg;  // covers hx + last segment + 1
+    const int pitch = row_pitch<T>(nx);  // covers hx + the x-solver's last chunk + 1
     const int rows = ny + 4;
     const long long fs = (long long)pitch * rows;
     // field stride: padded field rounded up to 256 bytes (the history ring is
@@ -305,7 +304,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     size_t o_fields = take(fb * nfields);
     size_t o_corner = take(cornerT.size() * sizeof(T));
     size_t o_gx = take(nx * sizeof(T)), o_gy = take(ny * sizeof(T));
-    size_t o_corr = take((size_t)(2 * nx + 2 * ny) * sizeof(T));
+    size_t o_corr = take((size_t)(4 * nx + 4 * ny + 4) * sizeof(T));
     size_t o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
     size_t o_comp = take(comp.size() * sizeof(double));
     size_t o_ctl = take(sizeof(Ctl)), o_coef = take(sizeof(Coef));
@@ -325,6 +324,11 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.eps = (T)eps;
     D.kahan = kahan ? 1 : 0;
     D.cross_mode = p.cross_mode;
+    D.tune_ykch = p.tune[0] == 8 || p.tune[0] == 16 || p.tune[0] == 32 ? p.tune[0] : 0;
+    D.tune_ythreads = p.tune[1] >= 32 && p.tune[1] <= 512 ? p.tune[1] : 0;
+    D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
+    D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
+    D.tune_xtma = (p.tune[2] & 2) ? 1 : 0;
     for (int s = 0; s < 4; s++) D.bc[s] = bt[s];
     D.cfl = p.cfl; D.ema_alpha = p.ema_alpha; D.dt_init = p.dt_init; D.dt_min = p.dt_min;
     D.dt_max = p.dt_max; D.ramp_time = p.ramp_time;
@@ -345,6 +349,8 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.gy = (T *)(base + o_gy);
     T *corr = (T *)(base + o_corr);
     D.corrW = corr; D.corrE = corr + ny; D.corrS = corr + 2 * ny; D.corrN = corr + 2 * ny + nx;
+    T *mq = corr + 2 * ny + 2 * nx;
+    D.mqW = mq; D.mqE = mq + ny; D.mqS = mq + 2 * ny; D.mqN = mq + 2 * ny + (nx + 2);
     double *cb = (double *)(base + o_cb);
     D.cW = cb; D.cE = cb + ny; D.cS = cb + 2 * ny; D.cN = cb + 2 * ny + nx;
     double *cp = (double *)(base + o_comp);
@@ -414,6 +420,7 @@ extern "C" bsq_status bsq_create(const bsq_params *p, const double *bed_corners,
         if (maker && (b.n_comp <= 0 || !b.amp || !b.freq || !b.phase || !b.dir)) return BSQ_ERR_ARG;
         if (b.n_comp < 0) return BSQ_ERR_ARG;
     }
+    cudaGetLastError();  // a failed call of another domain must not be reported here
     bsq_domain *d = new (std::nothrow) bsq_domain;
     if (!d) return BSQ_ERR_OOM;
     memset((void *)d, 0, sizeof(*d));
@@ -477,10 +484,22 @@ extern "C" size_t bsq_device_bytes(const bsq_domain *d) { return d ? d->dbytes :
 
 // ------------------------------------------------------------------ stepping
 
-static cudaError_t enqueue_step(bsq_domain *d, double forced_dt)
+// One step; its own dt was set by the previous step or the prologue, and
+// forced_dt_next (> 0) fixes the next one.
+static cudaError_t enqueue_step(bsq_domain *d, double forced_dt_next)
 {
-    return d->fp64 ? launch_step<double>(d->Dd, d->stream, forced_dt)
-                   : launch_step<float>(d->Df, d->stream, forced_dt);
+    return d->fp64 ? launch_step<double>(d->Dd, d->stream, forced_dt_next)
+                   : launch_step<float>(d->Df, d->stream, forced_dt_next);
+}
+
+// Limits of the run, then the controller of the first step (forced_dt > 0:
+// that step size).
+static cudaError_t enqueue_start(bsq_domain *d, double t_end, long long max_steps, double forced_dt)
+{
+    cudaError_t e = launch_set_limits(d->ctl, d->stream, t_end, max_steps);
+    if (e != cudaSuccess) return e;
+    return d->fp64 ? launch_prologue<double>(d->Dd, d->stream, forced_dt)
+                   : launch_prologue<float>(d->Df, d->stream, forced_dt);
 }
 
 static bsq_status read_ctl(const bsq_domain *d)
@@ -491,6 +510,7 @@ static bsq_status read_ctl(const bsq_domain *d)
 
 static bsq_status ctl_status(const Ctl &c)
 {
+    if (c.err & ERR_DEVICE_WAIT) return BSQ_ERR_TIMEOUT;
     if (c.err & ERR_NONFINITE) return BSQ_ERR_NONFINITE;
     if (c.err & (ERR_UNSTABLE | ERR_NODT)) return BSQ_ERR_UNSTABLE;
     return BSQ_OK;
@@ -513,6 +533,7 @@ static bsq_status build_graph(bsq_domain *d)
 
 extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done)
 {
+    cudaGetLastError();  // a failed call of another domain must not be reported here
     if (steps_done) *steps_done = 0;
     if (!d) return BSQ_ERR_ARG;
     if (d->sticky != BSQ_OK) return d->sticky;
@@ -520,8 +541,9 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
     bsq_status st = read_ctl(d);
     if (st != BSQ_OK) return set_sticky(d, st);
     const long long n0 = d->h_ctl->n;
-    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, t_end, max_steps)) return set_sticky(d, BSQ_ERR_CUDA);
     st = build_graph(d);
+    if (st != BSQ_OK) return set_sticky(d, st);
+    if (cudaSuccess != enqueue_start(d, t_end, max_steps, 0.0)) return set_sticky(d, BSQ_ERR_CUDA);
     if (st != BSQ_OK) return set_sticky(d, st);
     if (max_steps > 0) {
         long long ng = (max_steps + d->graph_steps - 1) / d->graph_steps;
@@ -557,13 +579,15 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
 
 extern "C" bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n)
 {
+    cudaGetLastError();  // a failed call of another domain must not be reported here
     if (!d || (n > 0 && !dts) || n < 0) return BSQ_ERR_ARG;
     if (d->sticky != BSQ_OK) return d->sticky;
     for (long long q = 0; q < n; q++)
         if (!(dts[q] > 0.0) || !isfinite(dts[q])) return BSQ_ERR_ARG;
-    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, INFINITY, 0)) return set_sticky(d, BSQ_ERR_CUDA);
+    if (n == 0) return BSQ_OK;
+    if (cudaSuccess != enqueue_start(d, INFINITY, 0, dts[0])) return set_sticky(d, BSQ_ERR_CUDA);
     for (long long q = 0; q < n; q++) {
-        if (enqueue_step(d, dts[q]) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+        if (enqueue_step(d, q + 1 < n ? dts[q + 1] : 0.0) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
         if ((q & 255) == 255) {
             bsq_status st = read_ctl(d);
             if (st != BSQ_OK) return set_sticky(d, st);
@@ -726,7 +750,7 @@ extern "C" bsq_status bsq_restore(bsq_domain *d, const void *buf, size_t len)
 
 // ------------------------------------------------------------------ profiling
 
-static const char *kKernelNames[] = {"ctl_ghost", "rhs_combine", "ysolve", "ghost_q", "xsolve"};
+static const char *kKernelNames[] = {"ghost", "rhs_combine", "ysolve", "ghost_q", "xsolve"};
 
 extern "C" const char *bsq_kernel_name(int k)
 {
@@ -742,7 +766,7 @@ extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, doub
         if (cudaEventCreate(&ev[k]) != cudaSuccess) return BSQ_ERR_CUDA;
     for (int k = 0; k < 5; k++) ms_out[k] = 0.0;
     bsq_status st = BSQ_OK;
-    if (cudaSuccess != launch_set_limits(d->ctl, d->stream, INFINITY, n_steps)) st = BSQ_ERR_CUDA;
+    if (cudaSuccess != enqueue_start(d, INFINITY, n_steps, 0.0)) st = BSQ_ERR_CUDA;
     for (long long q = 0; q < n_steps && st == BSQ_OK; q++) {
         cudaError_t e = d->fp64 ? launch_step_timed<double>(d->Dd, d->stream, 0.0, ev)
                                 : launch_step_timed<float>(d->Df, d->stream, 0.0, ev);

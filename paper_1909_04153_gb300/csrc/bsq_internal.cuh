@@ -12,7 +12,7 @@ enum { WALL = 0, SPONGE = 1, MAKER = 2 };
 enum { SW = 0, SE = 1, SS = 2, SN = 3 };
 
 // error flags raised on the device
-enum : unsigned { ERR_NONFINITE = 1u, ERR_UNSTABLE = 2u, ERR_NODT = 4u };
+enum : unsigned { ERR_NONFINITE = 1u, ERR_UNSTABLE = 2u, ERR_NODT = 4u, ERR_DEVICE_WAIT = 8u };
 
 // Controller state of one domain (FP64, device resident).  The controller
 // kernel reads it; the first block of the stencil kernel commits the step.
@@ -26,7 +26,7 @@ struct Ctl {
     unsigned long long rate_bits;  // Eq. 22 rate of the current state (bits of a positive double)
     unsigned long long clamps;     // positivity clamps so far
     unsigned int err;
-    int pad;
+    unsigned int done_count;  // x-solver blocks finished in the current step
 };
 
 // Per-step coefficients written by the controller, read by the step kernels.
@@ -37,6 +37,7 @@ struct Coef {
     int wc;                   // index of the w buffer holding level n
     long long n;
     double t0, t1, dt;
+    double ramp0, ramp1;      // wave-maker ramp r(t) at t_n and t_{n+1}
     double beta[3], gam[3];
     float betaf[3], gamf[3];
 };
@@ -52,6 +53,9 @@ struct Dev {
     double dxd, dyd;          // cell sizes in FP64 (wave-maker phases)
     T g, Bd, eps, w_s, friction, theta;
     int kahan, cross_mode;
+    int tune_ykch, tune_ythreads;  // y-solver chunk rows and block size (0: default)
+    int tune_rhs, tune_rows;       // RHS kernel variant (0 sliding window, 1 tiled), rows per warp
+    int tune_xtma;                 // 0: TMA-staged x-solver when it fits, 1: register version
     int bc[4];
     // controller inputs (FP64)
     double cfl, ema_alpha, dt_init, dt_min, dt_max;
@@ -70,6 +74,7 @@ struct Dev {
     T *gx, *gy;               // sponge factor profiles along x and y (product of sides)
     const double *cW, *cE, *cS, *cN;  // raw boundary coefficients for maker rows
     T *corrW, *corrE, *corrS, *corrN; // per-step maker corrections of the line right-hand sides
+    T *mqW, *mqE, *mqS, *mqN;         // maker Q at t_{n+1}: W/E per row, S/N per column -1..nx
     // wave maker
     int ncomp;
     const double *amp, *om, *kx, *ky, *ph, *cx, *cy;

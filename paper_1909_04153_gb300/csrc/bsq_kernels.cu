@@ -51,7 +51,15 @@ __device__ __forceinline__ T minmod3(T a, T b, T c)
 template <typename T>
 __device__ __forceinline__ T gslope(T qm, T q0, T qp, T th)
 {
-    return minmod3(th * (q0 - qm), (T)0.5 * (qp - qm), th * (qp - q0));
+    T a = q0 - qm, c = qp - q0;
+    if (th == (T)1) {
+        // theta = 1: the centred difference (a + c)/2 lies between a and c, so
+        // the minmod of the three equals the minmod of a and c (bitwise)
+        if (a > (T)0 && c > (T)0) return tmin(a, c);
+        if (a < (T)0 && c < (T)0) return tmax(a, c);
+        return (T)0;
+    }
+    return minmod3(th * a, (T)0.5 * (qp - qm), th * c);
 }
 
 // 1 / sqrt(h^4 + max(h^4, eps)) of the desingularised velocity of KP07,
@@ -66,11 +74,17 @@ __device__ __forceinline__ T desing_inv(T h, T eps)
 
 #define BSQ_SQRT2 1.41421356237309504880
 
-// Linear wave-maker state (eta, P, Q) at (x, y, t), all in FP64.
+// Wave-maker ramp r(t) = tanh(3 t / ramp_time) (1 without a ramp).
 template <typename T>
-__device__ void maker_state(const Dev<T> &D, double x, double y, double t, double &e, double &p, double &q)
+__device__ double maker_ramp(const Dev<T> &D, double t)
 {
-    double r = D.ramp_time > 0.0 ? tanh(3.0 * t / D.ramp_time) : 1.0;
+    return D.ramp_time > 0.0 ? tanh(3.0 * t / D.ramp_time) : 1.0;
+}
+
+// Linear wave-maker state (eta, P, Q) at (x, y, t) with ramp value r, in FP64.
+template <typename T>
+__device__ void maker_state(const Dev<T> &D, double x, double y, double t, double r, double &e, double &p, double &q)
+{
     double se = 0.0, sp = 0.0, sq = 0.0;
     for (int k = 0; k < D.ncomp; k++) {
         double ek = D.amp[k] * cos(D.kx[k] * x + D.ky[k] * y - D.om[k] * t + D.ph[k]);
@@ -149,7 +163,40 @@ __device__ void controller(const Dev<T> &D, double forced_dt, Coef &cf, unsigned
     for (int k = 0; k < 3; k++) { cf.betaf[k] = (float)cf.beta[k]; cf.gamf[k] = (float)cf.gam[k]; }
     cf.dt = dt;
     cf.t1 = t + dt;
+    cf.ramp0 = maker_ramp(D, cf.t0);
+    cf.ramp1 = maker_ramp(D, cf.t1);
     cf.active = 1;
+}
+
+// Controller for the step about to start (one thread); forced_dt > 0 replays a step size.
+template <typename T>
+__global__ void k_prologue(Dev<T> D, double forced_dt)
+{
+    Coef cf;
+    unsigned err;
+    controller(D, forced_dt, cf, err);
+    *D.coef = cf;
+    if (err) atomicOr(&D.ctl->err, err);
+    D.ctl->done_count = 0u;
+}
+
+// End of a step, in the last x-solver block to finish (thread 0 only, after
+// this block's atomicMax of the rate): the Eq. 22 rate of the new state is then
+// complete, so the controller of the next step runs here.
+template <typename T>
+__device__ void next_step_controller(const Dev<T> &D, double forced_dt_next)
+{
+    __threadfence();
+    const unsigned ticket = atomicAdd(&D.ctl->done_count, 1u);
+    if (ticket == gridDim.x - 1) {
+        __threadfence();
+        Coef cf;
+        unsigned err;
+        controller(D, forced_dt_next, cf, err);
+        *D.coef = cf;
+        if (err) atomicOr(&D.ctl->err, err);
+        D.ctl->done_count = 0u;
+    }
 }
 
 template <typename T> __device__ __forceinline__ T coefv(const Coef &c, int which, int k);
@@ -168,7 +215,7 @@ template <> __device__ __forceinline__ double coefv<double>(const Coef &c, int w
 // filled first (mirror with P negated, or the maker), then the S/N rows from
 // the filled columns (mirror with Q negated, or the maker).
 template <typename T>
-__device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t, T &gw, T &gP, T &gQ)
+__device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t, double ramp, T &gw, T &gP, T &gQ)
 {
     int nx = D.nx, ny = D.ny;
     int side = -1;
@@ -192,7 +239,7 @@ __device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t,
     }
     if (side >= 0) {
         double e, p, q;
-        maker_state(D, ((double)i + 0.5) * D.dxd, ((double)j + 0.5) * D.dyd, t, e, p, q);
+        maker_state(D, ((double)i + 0.5) * D.dxd, ((double)j + 0.5) * D.dyd, t, ramp, e, p, q);
         long long c = fidx(D, i, j);
         T b = D.bC[c];
         T d = tmax(D.w_s - b, (T)0);
@@ -208,26 +255,14 @@ __device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t,
     gQ = flipQ ? -D.Q[c] : D.Q[c];
 }
 
-// Controller + ghost fill at t_n + maker corrections of the line systems.
+// Ghost fill at t_n + maker corrections of the line systems (the controller of
+// this step ran at the end of the previous step, or in the prologue).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ctl_ghost(Dev<T> D, double forced_dt)
+__global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
 {
-    __shared__ Coef scf;
-    __shared__ unsigned serr;
-    if (threadIdx.x == 0) {
-        Coef cf;
-        unsigned err;
-        controller(D, forced_dt, cf, err);
-        scf = cf;
-        serr = err;
-        if (blockIdx.x == 0) {
-            *D.coef = cf;
-            if (err) atomicOr(&D.ctl->err, err);
-        }
-    }
-    __syncthreads();
+    const Coef scf = *D.coef;
     if (!scf.active) return;
-    const double t0 = scf.t0, t1 = scf.t1;
+    const double t0 = scf.t0, t1 = scf.t1, r0 = scf.ramp0, r1 = scf.ramp1;
     int nx = D.nx, ny = D.ny;
     T *w = D.w[scf.wc];
     long long nghost = 4LL * ny + 4LL * (nx + 4);
@@ -240,7 +275,7 @@ __global__ void __launch_bounds__(256) k_ctl_ghost(Dev<T> D, double forced_dt)
             int g = rem / ny + 1, j = rem % ny;
             int i = side == 0 ? -g : nx - 1 + g;
             T a, b, c;
-            ghost_value(D, w, i, j, t0, a, b, c);
+            ghost_value(D, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else if (idx < nghost) {
@@ -250,7 +285,7 @@ __global__ void __launch_bounds__(256) k_ctl_ghost(Dev<T> D, double forced_dt)
             int g = rem / (nx + 4) + 1, i = rem % (nx + 4) - 2;
             int j = side == 0 ? -g : ny - 1 + g;
             T a, b, c;
-            ghost_value(D, w, i, j, t0, a, b, c);
+            ghost_value(D, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else {
@@ -264,10 +299,11 @@ __global__ void __launch_bounds__(256) k_ctl_ghost(Dev<T> D, double forced_dt)
                     double x = side == 0 ? -0.5 * D.dxd : ((double)nx + 0.5) * D.dxd;
                     double y = ((double)j + 0.5) * D.dyd;
                     double e0, p0, q0, e1, p1, q1;
-                    maker_state(D, x, y, t0, e0, p0, q0);
-                    maker_state(D, x, y, t1, e1, p1, q1);
+                    maker_state(D, x, y, t0, r0, e0, p0, q0);
+                    maker_state(D, x, y, t1, r1, e1, p1, q1);
                     double a = side == 0 ? D.cW[j] : D.cE[j];
                     corr = (T)(-a * (p1 - p0));
+                    (side == 0 ? D.mqW : D.mqE)[j] = (T)q1;
                 }
                 (side == 0 ? D.corrW : D.corrE)[j] = corr;
             } else {
@@ -279,10 +315,17 @@ __global__ void __launch_bounds__(256) k_ctl_ghost(Dev<T> D, double forced_dt)
                     double x = ((double)i + 0.5) * D.dxd;
                     double y = side == 0 ? -0.5 * D.dyd : ((double)ny + 0.5) * D.dyd;
                     double e0, p0, q0, e1, p1, q1;
-                    maker_state(D, x, y, t0, e0, p0, q0);
-                    maker_state(D, x, y, t1, e1, p1, q1);
+                    maker_state(D, x, y, t0, r0, e0, p0, q0);
+                    maker_state(D, x, y, t1, r1, e1, p1, q1);
                     double a = side == 0 ? D.cS[i] : D.cN[i];
                     corr = (T)(-a * (q1 - q0));
+                    (side == 0 ? D.mqS : D.mqN)[i + 1] = (T)q1;
+                    if (i == 0 || i == nx - 1) {
+                        // the corner columns -1 and nx of the ghost row
+                        const int ic = i == 0 ? -1 : nx;
+                        maker_state(D, ((double)ic + 0.5) * D.dxd, y, t1, r1, e1, p1, q1);
+                        (side == 0 ? D.mqS : D.mqN)[ic + 1] = (T)q1;
+                    }
                 }
                 (side == 0 ? D.corrS : D.corrN)[i] = corr;
             }
@@ -317,7 +360,7 @@ __global__ void __launch_bounds__(256) k_ghost_q(Dev<T> D)
             j = side == 0 ? -g : ny - 1 + g;
         }
         T a, b, c;
-        ghost_value(D, w, i, j, cf.t1, a, b, c);
+        ghost_value(D, w, i, j, cf.t1, cf.ramp1, a, b, c);
         D.Q[fidx(D, i, j)] = c;
     }
 }
@@ -583,6 +626,300 @@ __global__ void __launch_bounds__(TX *TY) k_rhs_combine(Dev<T> D)
     }
 }
 
+// ------------------------------------------------------------------ RHS + combine, sliding window
+
+// Face state of KP07 on one side of a face: depth and desingularised velocities
+// and celerity; the discharges are recomputed as h u, h v.
+template <typename T>
+struct FaceSt {
+    T h, u, v, c;
+};
+
+__device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+
+template <typename T>
+__device__ __forceinline__ FaceSt<T> face_state(T wf, T Pf, T Qf, T bf, T g, T eps)
+{
+    FaceSt<T> s;
+    s.h = tmax(wf - bf, (T)0);
+    T iv = (T)BSQ_SQRT2 * s.h * desing_inv(s.h, eps);
+    s.u = iv * Pf;
+    s.v = iv * Qf;
+    s.c = tsqrt(g * s.h);
+    return s;
+}
+
+// Central-upwind flux from two face states; DIR 0: x-face, 1: y-face.
+template <typename T, int DIR>
+__device__ __forceinline__ void cu_flux_st(const FaceSt<T> &L, const FaceSt<T> &R, T g, T &H0, T &H1, T &H2)
+{
+    T unL = DIR == 0 ? L.u : L.v, unR = DIR == 0 ? R.u : R.v;
+    T ap = tmax(tmax(unL + L.c, unR + R.c), (T)0);
+    T am = tmin(tmin(unL - L.c, unR - R.c), (T)0);
+    T den = ap - am;
+    if (!(den > (T)0)) { H0 = H1 = H2 = (T)0; return; }
+    T inv = trcp(den);
+    T pL = L.h * L.u, qL = L.h * L.v, pR = R.h * R.u, qR = R.h * R.v;
+    T FL0, FL1, FL2, FR0, FR1, FR2;
+    if (DIR == 0) {
+        FL0 = pL; FL1 = pL * L.u + (T)0.5 * g * L.h * L.h; FL2 = qL * L.u;
+        FR0 = pR; FR1 = pR * R.u + (T)0.5 * g * R.h * R.h; FR2 = qR * R.u;
+    } else {
+        FL0 = qL; FL1 = pL * L.v; FL2 = qL * L.v + (T)0.5 * g * L.h * L.h;
+        FR0 = qR; FR1 = pR * R.v; FR2 = qR * R.v + (T)0.5 * g * R.h * R.h;
+    }
+    T k = ap * am * inv;
+    H0 = (ap * FL0 - am * FR0) * inv + k * (R.h - L.h);
+    H1 = (ap * FL1 - am * FR1) * inv + k * (pR - pL);
+    H2 = (ap * FL2 - am * FR2) * inv + k * (qR - qL);
+}
+
+template <typename T>
+__device__ __forceinline__ T shup(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <typename T>
+__device__ __forceinline__ T shdn(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+constexpr int SW_COLS = 28;  // interior columns per warp strip (lanes 2..29)
+
+// One warp walks a strip of 28 interior columns down ROWS rows.  Lane L holds
+// column i = i0 - 2 + L.  Windows of rows live in registers: w, P, Q at rows
+// r-3..r, eta at r-4..r, still depth at r-3..r, bed corners at r-2..r+1.  At
+// step r the leading row r is loaded, the y-reconstruction of row r-1 and the
+// y-face flux between rows r-2 and r-1 are formed, and row o = r-2 is finished:
+// x-reconstruction and x-face flux (neighbours by shuffles), bed source,
+// friction, dispersive differences (Eqs. 12-15) and the AB3 combine.  Every
+// reconstruction and every face flux is computed once per strip.
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    const int lane = threadIdx.x & 31;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int strip = wg % nstrip, band = wg / nstrip;
+    const int nx = D.nx, ny = D.ny;
+    const int j0 = band * ROWS;
+    if (j0 >= ny) return;
+    const int i = strip * SW_COLS - 2 + lane;           // this lane's column
+    const int ic = min(i, nx + 1);                       // clamped for loads
+    const int kc = min(i, nx + 2), kc1 = min(i + 1, nx + 2);
+    const bool lane_out = lane >= 2 && lane <= 29 && i < nx;
+    const T *w = D.w[cf.wc];
+    const T g = D.g, eps = D.eps, th = D.theta;
+    const T rdx = D.rdx, rdy = D.rdy, half_rdx = (T)0.5 * rdx, half_rdy = (T)0.5 * rdy;
+    const T rdx2 = rdx * rdx, rdy2 = rdy * rdy, q_rdxy = (T)0.25 * rdx * rdy;
+    const T c_xxx = (T)0.5 * rdx2 * rdx, c_yyy = (T)0.5 * rdy2 * rdy;
+    const T Bg = D.Bd * g, kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+    const T b0c = coefv<T>(cf, 0, 0), b1c = coefv<T>(cf, 0, 1), b2c = coefv<T>(cf, 0, 2);
+    const T g0c = coefv<T>(cf, 1, 0), g1c = coefv<T>(cf, 1, 1), g2c = coefv<T>(cf, 1, 2);
+    const bool extrap = D.cross_mode == 0;
+    const long long fs = D.fstride;
+    T *H = D.hist;
+    const T *corner = D.corner;
+    const int cp = D.cpitch;
+
+    // windows (index 3 = newest row)
+    T wW[4] = {0, 0, 0, 0}, PW[4] = {0, 0, 0, 0}, QW[4] = {0, 0, 0, 0};
+    T eW[5] = {0, 0, 0, 0, 0}, dW[4] = {0, 0, 0, 0}, bW[3] = {0, 0, 0};
+    T KW[4] = {0, 0, 0, 0}, KRW[4] = {0, 0, 0, 0};  // corners at columns i and i+1, rows r-2..r+1
+    FaceSt<T> Nprev = {0, 0, 0, 0};                  // N face state of row r-2
+    T Hy0 = 0, Hy1 = 0, Hy2 = 0;                     // y-flux below row r-2 (face (r-2)-1/2)
+    {
+        int rr = min(j0 - 2, ny + 2);
+        KW[3] = corner[(long long)(rr + 2) * cp + (kc + 2)];
+        KRW[3] = corner[(long long)(rr + 2) * cp + (kc1 + 2)];
+    }
+    unsigned long long nclamp = 0;
+    const int rend = min(j0 + ROWS, ny) + 2;
+    // software pipeline: the leading row and the history of the next output
+    // row are loaded one step ahead, so their latency overlaps the arithmetic
+    T pw, pP, pQ, pK, pKR;
+    auto load_lead = [&](int r) {
+        const int rr = min(r, ny + 1);
+        const long long cr = fidx(D, ic, rr);
+        const int kr = min(r + 1, ny + 2);
+        pw = w[cr]; pP = D.P[cr]; pQ = D.Q[cr];
+        pK = corner[(long long)(kr + 2) * cp + (kc + 2)];
+        pKR = corner[(long long)(kr + 2) * cp + (kc1 + 2)];
+    };
+    T hE1 = 0, hF1 = 0, hG1 = 0, hGs1 = 0, hFs1 = 0, hE2 = 0, hF2 = 0, hG2 = 0, hGs2 = 0, hFs2 = 0, hcw = 0;
+    auto load_hist = [&](int o) {
+        if (lane_out && o >= j0 && o < ny) {
+            const long long c = fidx(D, i, o);
+            if (D.kahan) hcw = D.cw[c];
+            if (cf.nlev >= 2) {
+                const long long oo = (long long)cf.s1 * fs + c;
+                hE1 = H[0 * 3 * fs + oo]; hF1 = H[1 * 3 * fs + oo]; hG1 = H[2 * 3 * fs + oo]; hGs1 = H[4 * 3 * fs + oo];
+                if (extrap) hFs1 = H[3 * 3 * fs + oo];
+            }
+            if (cf.nlev >= 3) {
+                const long long oo = (long long)cf.s2 * fs + c;
+                hE2 = H[0 * 3 * fs + oo]; hF2 = H[1 * 3 * fs + oo]; hG2 = H[2 * 3 * fs + oo]; hGs2 = H[4 * 3 * fs + oo];
+                if (extrap) hFs2 = H[3 * 3 * fs + oo];
+            }
+        }
+    };
+    load_lead(j0 - 2);
+    for (int r = j0 - 2; r < rend; r++) {
+        // ---- leading row r (prefetched), bed corners at row r+1
+        T wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR;
+        T cE1 = hE1, cF1 = hF1, cG1 = hG1, cGs1 = hGs1, cFs1 = hFs1;
+        T cE2 = hE2, cF2 = hF2, cG2 = hG2, cGs2 = hGs2, cFs2 = hFs2, ccw = hcw;
+        if (r + 1 < rend) load_lead(r + 1);
+        load_hist(r - 1);  // output row of the next step
+#pragma unroll
+        for (int q = 0; q < 3; q++) { wW[q] = wW[q + 1]; PW[q] = PW[q + 1]; QW[q] = QW[q + 1]; dW[q] = dW[q + 1]; KW[q] = KW[q + 1]; KRW[q] = KRW[q + 1]; }
+#pragma unroll
+        for (int q = 0; q < 4; q++) eW[q] = eW[q + 1];
+        bW[0] = bW[1]; bW[1] = bW[2];
+        wW[3] = wn; PW[3] = Pn; QW[3] = Qn; KW[3] = Kn; KRW[3] = KRn;
+        // cell-centre bed of row r (mean of its 4 face values), d, eta
+        {
+            T bw_ = (T)0.5 * (KW[2] + KW[3]), be_ = (T)0.5 * (KRW[2] + KRW[3]);
+            T bs_ = (T)0.5 * (KW[2] + KRW[2]), bn_ = (T)0.5 * (KW[3] + KRW[3]);
+            T bc = (T)0.25 * (bw_ + be_ + bs_ + bn_);
+            T d = tmax(D.w_s - bc, (T)0);
+            bW[2] = bc;
+            dW[3] = d;
+            eW[4] = tmax(wn - bc, (T)0) - d;
+        }
+        // ---- y-reconstruction of row r-1 (rows r-2, r-1, r) and the y-face flux
+        //      between rows r-2 and r-1
+        {
+            T bS = (T)0.5 * (KW[1] + KRW[1]), bN = (T)0.5 * (KW[2] + KRW[2]);
+            T wl, wh, Pl, Ph, Ql, Qh;
+            reconstruct(wW[1], wW[2], wW[3], PW[1], PW[2], PW[3], QW[1], QW[2], QW[3], bS, bN, th,
+                        wl, wh, Pl, Ph, Ql, Qh);
+            FaceSt<T> S = face_state(wl, Pl, Ql, bS, g, eps);
+            FaceSt<T> Nn = face_state(wh, Ph, Qh, bN, g, eps);
+            T h0, h1, h2;
+            cu_flux_st<T, 1>(Nprev, S, g, h0, h1, h2);  // face (r-1)-1/2 = o+1/2 for o = r-2
+            // ---- finish row o = r - 2
+            const int o = r - 2;
+            // x-reconstruction of row o needs w, P, Q of the lanes next door
+            T w0 = wW[1], P0 = PW[1], Q0 = QW[1];
+            T wm = shup(w0, 1), wp = shdn(w0, 1), Pm = shup(P0, 1), Pp = shdn(P0, 1);
+            T Qm = shup(Q0, 1), Qp = shdn(Q0, 1);
+            T bxW = (T)0.5 * (KW[0] + KW[1]), bxE = (T)0.5 * (KRW[0] + KRW[1]);
+            T xwl, xwh, xPl, xPh, xQl, xQh;
+            reconstruct(wm, w0, wp, Pm, P0, Pp, Qm, Q0, Qp, bxW, bxE, th, xwl, xwh, xPl, xPh, xQl, xQh);
+            FaceSt<T> Wst = face_state(xwl, xPl, xQl, bxW, g, eps);
+            FaceSt<T> Est = face_state(xwh, xPh, xQh, bxE, g, eps);
+            FaceSt<T> El;  // E state of the lane to the left
+            El.h = shup(Est.h, 1); El.u = shup(Est.u, 1); El.v = shup(Est.v, 1); El.c = shup(Est.c, 1);
+            T x0, x1, x2;
+            cu_flux_st<T, 0>(El, Wst, g, x0, x1, x2);  // face i-1/2
+            T xe0 = shdn(x0, 1), xe1 = shdn(x1, 1), xe2 = shdn(x2, 1);  // face i+1/2
+            // neighbours for the dispersive and cross terms
+            T em1 = shup(eW[2], 1), ep1 = shdn(eW[2], 1), em2 = shup(eW[2], 2), ep2 = shdn(eW[2], 2);
+            T eSm = shup(eW[1], 1), eSp = shdn(eW[1], 1), eNm = shup(eW[3], 1), eNp = shdn(eW[3], 1);
+            T dm = shup(dW[1], 1), dp = shdn(dW[1], 1);
+            T QSm = shup(QW[0], 1), QSp = shdn(QW[0], 1), QNm = shup(QW[2], 1), QNp = shdn(QW[2], 1);
+            T PSm = shup(PW[0], 1), PSp = shdn(PW[0], 1), PNm = shup(PW[2], 1), PNp = shdn(PW[2], 1);
+            if (lane_out && o >= j0 && o < ny) {
+                const long long c = fidx(D, i, o);
+                T divx0 = (xe0 - x0) * rdx, divx1 = (xe1 - x1) * rdx, divx2 = (xe2 - x2) * rdx;
+                T divy0 = (h0 - Hy0) * rdy, divy1 = (h1 - Hy1) * rdy, divy2 = (h2 - Hy2) * rdy;
+                T bS0 = (T)0.5 * (KW[0] + KRW[0]), bN0 = (T)0.5 * (KW[1] + KRW[1]);
+                T bc = bW[0];
+                T srcx = -g * (bxE - bxW) * rdx * (w0 - (T)0.5 * (bxE + bxW));
+                T srcy = -g * (bN0 - bS0) * rdy * (w0 - (T)0.5 * (bN0 + bS0));
+                T fr1 = (T)0, fr2 = (T)0;
+                if (D.friction != (T)0) {
+                    T h = tmax(w0 - bc, (T)0);
+                    T iv = (T)BSQ_SQRT2 * h * desing_inv(h, eps);
+                    T u = iv * P0, v = iv * Q0;
+                    T sp = tsqrt(u * u + v * v);
+                    fr1 = D.friction * u * sp;
+                    fr2 = D.friction * v * sp;
+                }
+                const T d = dW[1];
+                const T ddx = (dp - dm) * half_rdx;
+                const T ddy = (dW[2] - dW[0]) * half_rdy;
+                const T e0 = eW[2];
+                T e_xx = (ep1 - (T)2 * e0 + em1) * rdx2;
+                T e_yy = (eW[3] - (T)2 * e0 + eW[1]) * rdy2;
+                T e_xy = (eNp - eSp - eNm + eSm) * q_rdxy;
+                T e_xxx = (ep2 - (T)2 * ep1 + (T)2 * em1 - em2) * c_xxx;
+                T e_yyy = (eW[4] - (T)2 * eW[3] + (T)2 * eW[1] - eW[0]) * c_yyy;
+                T eyy_p = (eNp - (T)2 * ep1 + eSp) * rdy2;
+                T eyy_m = (eNm - (T)2 * em1 + eSm) * rdy2;
+                T exx_p = (eNp - (T)2 * eW[3] + eNm) * rdx2;
+                T exx_m = (eSp - (T)2 * eW[1] + eSm) * rdx2;
+                T e_xyy = (eyy_p - eyy_m) * half_rdx;
+                T e_xxy = (exx_p - exx_m) * half_rdy;
+                T dispx = Bg * d * d * d * (e_xxx + e_xyy) + Bg * d * d * (ddx * ((T)2 * e_xx + e_yy) + ddy * e_xy);
+                T dispy = Bg * d * d * d * (e_yyy + e_xxy) + Bg * d * d * (ddy * ((T)2 * e_yy + e_xx) + ddx * e_xy);
+                T E = -divx0 - divy0;
+                T F = -divx1 - divy1 + srcx - fr1 + dispx;
+                T G = -divx2 - divy2 + srcy - fr2 + dispy;
+                T Q_x = (Qp - Qm) * half_rdx;
+                T Q_y = (QW[2] - QW[0]) * half_rdy;
+                T Q_xy = (QNp - QSp - QNm + QSm) * q_rdxy;
+                T P_x = (Pp - Pm) * half_rdx;
+                T P_y = (PW[2] - PW[0]) * half_rdy;
+                T P_xy = (PNp - PSp - PNm + PSm) * q_rdxy;
+                T Fs = d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+                T Gs = d * ddy * P_x * sixth + d * ddx * P_y * sixth + kB * d * d * P_xy;
+                // AB3 / Euler combine (Eqs. 42-43), history prefetched one step ahead
+                T dw = b0c * E, dU = b0c * F, dV = b0c * G + g0c * Gs;
+                if (extrap) dU += g0c * Fs;
+                if (cf.nlev >= 2) {
+                    dw += b1c * cE1;
+                    dU += b1c * cF1;
+                    dV += b1c * cG1 + g1c * cGs1;
+                    if (extrap) dU += g1c * cFs1;
+                }
+                if (cf.nlev >= 3) {
+                    dw += b2c * cE2;
+                    dU += b2c * cF2;
+                    dV += b2c * cG2 + g2c * cGs2;
+                    if (extrap) dU += g2c * cFs2;
+                }
+                if (!extrap) dU -= Fs;
+                {
+                    const long long oo = (long long)cf.s0 * fs + c;
+                    H[0 * 3 * fs + oo] = E;
+                    H[1 * 3 * fs + oo] = F;
+                    H[2 * 3 * fs + oo] = G;
+                    if (extrap) H[3 * 3 * fs + oo] = Fs;
+                    H[4 * 3 * fs + oo] = Gs;
+                }
+                T wnew, cwn = (T)0;
+                if (D.kahan) {
+                    T y = dw - ccw;
+                    wnew = w0 + y;
+                    cwn = (wnew - w0) - y;
+                } else {
+                    wnew = w0 + dw;
+                }
+                if (wnew < bc) { wnew = bc; cwn = (T)0; nclamp++; }
+                D.w[cf.wc ^ 1][c] = wnew;
+                if (D.kahan) D.cw[c] = cwn;
+                D.dU[c] = dU;
+                D.dV[c] = dV;
+            }
+            Nprev = Nn;
+            Hy0 = h0; Hy1 = h1; Hy2 = h2;
+        }
+    }
+    // positivity clamps: warp total, one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) nclamp += __shfl_xor_sync(0xffffffffu, nclamp, o);
+    if (lane == 0 && nclamp) atomicAdd(&D.ctl->clamps, nclamp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // commit the step in the controller state (the controller kernel of
+        // this step has finished; no thread of this kernel reads Ctl)
+        Ctl *ct = D.ctl;
+        ct->dtm2 = ct->dtm1;
+        ct->dtm1 = cf.dt;
+        ct->last_dt = cf.dt;
+        ct->t = cf.t1;
+        ct->n = cf.n + 1;
+        ct->rate_bits = 0ull;
+    }
+}
+
 // ------------------------------------------------------------------ y-line solves
 
 // Thread (column c, chunk k) owns rows [k*KCH, (k+1)*KCH) of one column.
@@ -591,7 +928,7 @@ __global__ void __launch_bounds__(TX *TY) k_rhs_combine(Dev<T> D)
 // chunk, a block scan over the chunks of a column supplies the value entering
 // each chunk, and the chunk is finished from registers.
 template <typename T, int KCH>
-__global__ void k_ysolve(Dev<T> D, int CW, int NCH)
+__global__ void __launch_bounds__(512, 2) k_ysolve(Dev<T> D, int CW, int NCH)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
@@ -709,192 +1046,550 @@ __device__ __forceinline__ void vstore(T *p, const T *in)
     for (int q = 0; q < VecT<T>::N; q++) s[q] = in[q];
     *reinterpret_cast<V *>(p) = v;
 }
-
-// Row segment of VEC elements per lane plus one neighbour on each side.
-template <typename T, int VEC>
-__device__ __forceinline__ void load_halo_row(const T *row, int ibase, int lane, T *v)
+template <typename T, int K>
+__device__ __forceinline__ void vload_k(const T *p, T *out)
 {
-    vload(row + ibase, v + 1);
-    T left = __shfl_up_sync(0xffffffffu, v[VEC], 1);
-    T right = __shfl_down_sync(0xffffffffu, v[1], 1);
-    if (lane == 0) left = row[ibase - 1];
-    if (lane == 31) right = row[ibase + VEC];
-    v[0] = left;
-    v[VEC + 1] = right;
+#pragma unroll
+    for (int v = 0; v < K; v += VecT<T>::N) vload(p + v, out + v);
+}
+template <typename T, int K>
+__device__ __forceinline__ void vstore_k(T *p, const T *in)
+{
+#pragma unroll
+    for (int v = 0; v < K; v += VecT<T>::N) vstore(p + v, in + v);
 }
 
-template <typename T>
-__global__ void k_xsolve(Dev<T> D, int nseg)
+// K contiguous elements of a row starting at ib, plus one neighbour on each
+// side (v[0] and v[K+1]); neighbours come from the adjacent lanes, and from
+// memory at the ends of a warp.
+template <typename T, int K>
+__device__ __forceinline__ void load_halo_chunk(const T *row, int ib, int lane, T *v)
+{
+    vload_k<T, K>(row + ib, v + 1);
+    T left = __shfl_up_sync(0xffffffffu, v[K], 1);
+    T right = __shfl_down_sync(0xffffffffu, v[1], 1);
+    if (lane == 0) left = row[ib - 1];
+    if (lane == 31) right = row[ib + K];
+    v[0] = left;
+    v[K + 1] = right;
+}
+
+// One CTA per x-line (Eq. 19).  Thread t owns the K contiguous elements
+// [K t, K t + K) in registers.  Forward elimination y_i = m_i r_i + e_i y_{i-1}
+// and back substitution x_i = y_i - c'_i x_{i+1} are affine recurrences: each
+// thread composes its chunk, a block scan (warp shuffles, then across warps in
+// shared memory) gives the value entering each chunk, and the chunk is
+// finished in registers.  Also: F* at the new level from Q^{n+1} on the
+// right-hand side (sequential cross form), compensated P update, sponge on w
+// and P, and the Eq. 22 rate of the finished state (one atomic per block).
+template <typename T, int K>
+__global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
-    constexpr int VEC = VecT<T>::N;
-    constexpr int SEG = 32 * VEC;
-    extern __shared__ unsigned char smem_raw[];
-    T *ybuf = reinterpret_cast<T *>(smem_raw) + (size_t)threadIdx.y * nseg * SEG;
-    __shared__ double wmax[32];
-    const int lane = threadIdx.x;
-    const int j = blockIdx.x * blockDim.y + threadIdx.y;
-    const int nx = D.nx, ny = D.ny;
-    const bool rowok = j < ny;
-    const int jr = rowok ? j : ny - 1;  // keep loads in bounds for idle rows
-    const long long rowo = fidx(D, 0, jr);
-    const T *dUr = D.dU + rowo, *mr = D.fxm + rowo, *er = D.fxe + rowo, *cr = D.fxc + rowo;
+    __shared__ T sA[32], sB[32];
+    __shared__ double smax[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int j = blockIdx.x;
+    const int nx = D.nx;
+    const int ib = t * K;
+    const long long rowo = fidx(D, 0, j);
     const bool seq = D.cross_mode != 0;
-    const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
-    const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
-    const T corrW = D.corrW[jr], corrE = D.corrE[jr];
 
-    // forward elimination, segment by segment, carry = y at the last element
-    T carry = (T)0;
-    for (int s = 0; s < nseg; s++) {
-        const int ib = s * SEG + lane * VEC;
-        T r[VEC], m[VEC], e[VEC];
-        vload(dUr + ib, r);
-        vload(mr + ib, m);
-        vload(er + ib, e);
-        if (seq) {
-            // F* of Eq. 14 at the new level from Q^{n+1} (ghosts at t_{n+1})
-            T q0[VEC + 2], qm[VEC + 2], qp[VEC + 2], b0[VEC + 2], bm[VEC + 2], bp[VEC + 2];
-            load_halo_row<T, VEC>(D.Q + rowo, ib, lane, q0);
-            load_halo_row<T, VEC>(D.Q + rowo - D.pitch, ib, lane, qm);
-            load_halo_row<T, VEC>(D.Q + rowo + D.pitch, ib, lane, qp);
-            load_halo_row<T, VEC>(D.bC + rowo, ib, lane, b0);
-            load_halo_row<T, VEC>(D.bC + rowo - D.pitch, ib, lane, bm);
-            load_halo_row<T, VEC>(D.bC + rowo + D.pitch, ib, lane, bp);
+    T r[K], m[K], e[K];
+    vload_k<T, K>(D.dU + rowo + ib, r);
+    vload_k<T, K>(D.fxm + rowo + ib, m);
+    vload_k<T, K>(D.fxe + rowo + ib, e);
+    if (seq) {
+        // F* of Eq. 14 at the new level from Q^{n+1} (ghosts at t_{n+1})
+        const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+        const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+        T dd[K + 2], ddy[K];
+        {
+            T b0[K + 2], bm[K + 2], bp[K + 2];
+            load_halo_chunk<T, K>(D.bC + rowo, ib, lane, b0);
+            load_halo_chunk<T, K>(D.bC + rowo - D.pitch, ib, lane, bm);
+            load_halo_chunk<T, K>(D.bC + rowo + D.pitch, ib, lane, bp);
 #pragma unroll
-            for (int q = 0; q < VEC; q++) {
-                T d = tmax(D.w_s - b0[q + 1], (T)0);
-                T ddx = (tmax(D.w_s - b0[q + 2], (T)0) - tmax(D.w_s - b0[q], (T)0)) * half_rdx;
-                T ddy = (tmax(D.w_s - bp[q + 1], (T)0) - tmax(D.w_s - bm[q + 1], (T)0)) * half_rdy;
-                T Q_x = (q0[q + 2] - q0[q]) * half_rdx;
-                T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
-                T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
-                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
-            }
+            for (int q = 0; q < K + 2; q++) dd[q] = tmax(D.w_s - b0[q], (T)0);
+#pragma unroll
+            for (int q = 0; q < K; q++)
+                ddy[q] = (tmax(D.w_s - bp[q + 1], (T)0) - tmax(D.w_s - bm[q + 1], (T)0)) * half_rdy;
         }
+        T q0[K + 2], qm[K + 2], qp[K + 2];
+        load_halo_chunk<T, K>(D.Q + rowo, ib, lane, q0);
+        load_halo_chunk<T, K>(D.Q + rowo - D.pitch, ib, lane, qm);
+        load_halo_chunk<T, K>(D.Q + rowo + D.pitch, ib, lane, qp);
 #pragma unroll
-        for (int q = 0; q < VEC; q++) {
-            int i = ib + q;
-            if (i == 0) r[q] += corrW;
-            if (i == nx - 1) r[q] += corrE;
-            if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
+        for (int q = 0; q < K; q++) {
+            T d = dd[q + 1];
+            T ddx = (dd[q + 2] - dd[q]) * half_rdx;
+            T Q_x = (q0[q + 2] - q0[q]) * half_rdx;
+            T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+            T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+            r[q] += d * ddx * Q_y * sixth + d * ddy[q] * Q_x * sixth + kB * d * d * Q_xy;
         }
-        T A = (T)1, B = (T)0;
+    }
+    const T corrW = D.corrW[j], corrE = D.corrE[j];
 #pragma unroll
-        for (int q = 0; q < VEC; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
-        // inclusive warp scan, lower lanes first
+    for (int q = 0; q < K; q++) {
+        int i = ib + q;
+        if (i == 0) r[q] += corrW;
+        if (i == nx - 1) r[q] += corrE;
+        if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
+    }
+    // ---- forward elimination: compose, block scan (earlier chunks first)
+    T A = (T)1, B = (T)0;
+#pragma unroll
+    for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T Ap = __shfl_up_sync(0xffffffffu, A, o);
+        T Bp = __shfl_up_sync(0xffffffffu, B, o);
+        if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+    }
+    if (lane == 31) { sA[wid] = A; sB[wid] = B; }
+    T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) { Ae = (T)1; Be = (T)0; }
+    __syncthreads();
+    if (wid == 0) {
+        T a = lane < nw ? sA[lane] : (T)1, b = lane < nw ? sB[lane] : (T)0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            T Ap = __shfl_up_sync(0xffffffffu, A, o);
-            T Bp = __shfl_up_sync(0xffffffffu, B, o);
-            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+            T ap = __shfl_up_sync(0xffffffffu, a, o);
+            T bp = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { b = a * bp + b; a = a * ap; }
         }
-        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-        if (lane == 0) { Ae = (T)1; Be = (T)0; }
-        T y = Ae * carry + Be;
-#pragma unroll
-        for (int q = 0; q < VEC; q++) { y = m[q] * r[q] + e[q] * y; r[q] = y; }
-        vstore(ybuf + ib, r);
-        carry = __shfl_sync(0xffffffffu, y, 31);
+        T bx = __shfl_up_sync(0xffffffffu, b, 1);
+        if (lane == 0) bx = (T)0;
+        if (lane < nw) sB[lane] = bx;  // y entering warp `lane`
     }
-    __syncwarp();
+    __syncthreads();
+    T y = Ae * sB[wid] + Be;
+#pragma unroll
+    for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
+    __syncthreads();  // sA/sB reused below
 
-    // back substitution from the last segment, carry = x at the first element
-    T xcarry = (T)0;
-    T rate = (T)0;
-    bool bad = false;
+    // ---- back substitution: compose from the end, block suffix scan
+    T c[K];
+    vload_k<T, K>(D.fxc + rowo + ib, c);
+#pragma unroll
+    for (int q = 0; q < K; q++)
+        if (ib + q >= nx) c[q] = (T)0;
+    T al = (T)0, be = (T)1;
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T ap = __shfl_down_sync(0xffffffffu, al, o);
+        T bp = __shfl_down_sync(0xffffffffu, be, o);
+        if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+    }
+    if (lane == 0) { sA[wid] = al; sB[wid] = be; }
+    T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
+    if (lane == 31) { an = (T)0; bn = (T)1; }
+    __syncthreads();
+    if (wid == 0) {
+        T a = lane < nw ? sA[lane] : (T)0, b = lane < nw ? sB[lane] : (T)1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, a, o);
+            T bp = __shfl_down_sync(0xffffffffu, b, o);
+            if (lane + o < 32) { a = a + b * ap; b = b * bp; }
+        }
+        T ax = __shfl_down_sync(0xffffffffu, a, 1);
+        if (lane == 31) ax = (T)0;
+        if (lane < nw) sA[lane] = ax;  // x just after warp `lane`
+    }
+    __syncthreads();
+    T x = an + bn * sA[wid];
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
+
+    // ---- P^{n+1} = P^n + x (compensated), sponge on w and P, Eq. 22 rate
     T *Pr = D.P + rowo, *cPr = D.cP + rowo;
     T *wr = D.w[cf.wc ^ 1] + rowo, *cwr = D.cw + rowo;
-    const T *Qr = D.Q + rowo, *bCr = D.bC + rowo;
-    const T gyj = D.gy[jr];
-    for (int s = nseg - 1; s >= 0; s--) {
-        const int ib = s * SEG + lane * VEC;
-        T y[VEC], cc[VEC];
-        vload(ybuf + ib, y);
-        vload(cr + ib, cc);
+    T Pv[K], cPv[K], wv[K], Qv[K], bv[K];
+    vload_k<T, K>(Pr + ib, Pv);
+    if (D.kahan) vload_k<T, K>(cPr + ib, cPv);
+    vload_k<T, K>(wr + ib, wv);
+    vload_k<T, K>(D.Q + rowo + ib, Qv);
+    vload_k<T, K>(D.bC + rowo + ib, bv);
+    const T gyj = D.gy[j];
+    T rate = (T)0;
+    bool bad = false;
 #pragma unroll
-        for (int q = 0; q < VEC; q++)
-            if (ib + q >= nx) { y[q] = (T)0; cc[q] = (T)0; }
-        // lane map: x_first = al + be * x_after
-        T al = (T)0, be = (T)1;
-#pragma unroll
-        for (int q = VEC - 1; q >= 0; q--) { al = y[q] - cc[q] * al; be = -cc[q] * be; }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T ap = __shfl_down_sync(0xffffffffu, al, o);
-            T bp = __shfl_down_sync(0xffffffffu, be, o);
-            if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+    for (int q = 0; q < K; q++) {
+        const int i = ib + q;
+        if (i >= nx) continue;
+        T Pn, cn = (T)0;
+        if (D.kahan) {
+            T yy = r[q] - cPv[q];
+            Pn = Pv[q] + yy;
+            cn = (Pn - Pv[q]) - yy;
+        } else {
+            Pn = Pv[q] + r[q];
         }
-        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
-        if (lane == 31) { an = (T)0; bn = (T)1; }
-        T x = an + bn * xcarry;
-        T xs[VEC];
-#pragma unroll
-        for (int q = VEC - 1; q >= 0; q--) { x = y[q] - cc[q] * x; xs[q] = x; }
-        xcarry = __shfl_sync(0xffffffffu, xs[0], 0);
-
-        // P^{n+1} = P^n + x (compensated), sponge on w and P, Eq. 22 rate
-        if (rowok) {
-            T Pv[VEC], cPv[VEC], wv[VEC], Qv[VEC], bv[VEC];
-            vload(Pr + ib, Pv);
-            if (D.kahan) vload(cPr + ib, cPv);
-            vload(wr + ib, wv);
-            vload(Qr + ib, Qv);
-            vload(bCr + ib, bv);
-#pragma unroll
-            for (int q = 0; q < VEC; q++) {
-                const int i = ib + q;
-                if (i >= nx) continue;
-                T Pn, cn = (T)0;
-                if (D.kahan) {
-                    T yy = xs[q] - cPv[q];
-                    Pn = Pv[q] + yy;
-                    cn = (Pn - Pv[q]) - yy;
-                } else {
-                    Pn = Pv[q] + xs[q];
-                }
-                T wq = wv[q];
-                T gm = D.gx[i] * gyj;
-                if (gm < (T)1) {
-                    T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
-                    wq = bv[q] + (d + gm * (h - d));
-                    wr[i] = wq;
-                    if (D.kahan) cwr[i] = (T)0;
-                    Pn *= gm;
-                    cn *= gm;
-                }
-                Pv[q] = Pn;
-                cPv[q] = cn;
-                T h = tmax(wq - bv[q], (T)0);
-                T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-                T u = iv * Pn, v = iv * Qv[q];
-                T cc2 = tsqrt(D.g * h);
-                T rq = tmax((fabs(u) + cc2) * D.rdx, (fabs(v) + cc2) * D.rdy);
-                rate = tmax(rate, rq);
-                if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
-            }
-            vstore(Pr + ib, Pv);
-            if (D.kahan) vstore(cPr + ib, cPv);
+        T wq = wv[q];
+        T gm = D.gx[i] * gyj;
+        if (gm < (T)1) {
+            T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
+            wq = bv[q] + (d + gm * (h - d));
+            wr[i] = wq;
+            if (D.kahan) cwr[i] = (T)0;
+            Pn *= gm;
+            cn *= gm;
         }
+        Pv[q] = Pn;
+        cPv[q] = cn;
+        T h = tmax(wq - bv[q], (T)0);
+        T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
+        T u = iv * Pn, v = iv * Qv[q];
+        T cc = tsqrt(D.g * h);
+        rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+        if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
     }
-    // block max of the rate, one atomic per block
+    vstore_k<T, K>(Pr + ib, Pv);
+    if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+
     double rr = (double)rate;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
     bool anybad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) wmax[threadIdx.y] = anybad ? -1.0 : rr;
+    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
     __syncthreads();
-    if (threadIdx.y == 0 && lane == 0) {
+    if (t == 0) {
         double mx = 0.0;
         bool fl = false;
-        for (int q = 0; q < (int)blockDim.y; q++) {
-            if (wmax[q] < 0.0) fl = true;
-            else mx = fmax(mx, wmax[q]);
+        for (int q = 0; q < nw; q++) {
+            if (smax[q] < 0.0) fl = true;
+            else mx = fmax(mx, smax[q]);
         }
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
+        next_step_controller(D, forced_dt_next);
     }
+}
+
+// ------------------------------------------------------------------ x-line solves, TMA-staged
+
+// Shared-memory address of a generic pointer (for PTX operands).
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// 1D bulk copy global -> shared, completion counted on the mbarrier (TMA)
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity`; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, long long limit)
+{
+    for (long long it = 0; it < limit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Same arithmetic as k_xsolve; the row's 13 input arrays are staged in shared
+// memory by bulk asynchronous copies issued by one thread, so the whole row's
+// loads are in flight at once.  Staged: dU, m, e, c', P, cP, w (interior
+// span) and Q, bC at rows j-1, j, j+1 (interior span plus one 16-byte halo
+// on each side).
+constexpr int XT_ARR_PLAIN = 7, XT_ARR_HALO = 6;
+
+template <typename T, int K>
+__global__ void __launch_bounds__(512) k_xsolve_tma(Dev<T> D, int span, double forced_dt_next)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ T sA[32], sB[32];
+    __shared__ double smax[32];
+    const int hx = D.hx;
+    const int hspan = span + 2 * hx;  // halo arrays: columns -hx .. span+hx-1
+    T *S = reinterpret_cast<T *>(smem_raw);
+    T *sdU = S, *sm = S + span, *se = S + 2 * span, *sc = S + 3 * span, *sP = S + 4 * span;
+    T *scP = S + 5 * span, *sw = S + 6 * span;
+    T *sH = S + 7 * span;  // Q(j), Q(j-1), Q(j+1), bC(j), bC(j-1), bC(j+1), each hspan long
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int j = blockIdx.x;
+    const int nx = D.nx;
+    const long long rowo = fidx(D, 0, j);
+    const bool seq = D.cross_mode != 0;
+    T *wrow = D.w[cf.wc ^ 1] + rowo;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+        const unsigned pb = (unsigned)(span * sizeof(T)), hb = (unsigned)(hspan * sizeof(T));
+        unsigned total = 6u * pb + (D.kahan ? pb : 0u) + (seq ? 6u * hb : 0u);
+        mbar_expect_tx(&bar, total);
+        tma_load_1d(sdU, D.dU + rowo, pb, &bar);
+        tma_load_1d(sm, D.fxm + rowo, pb, &bar);
+        tma_load_1d(se, D.fxe + rowo, pb, &bar);
+        tma_load_1d(sc, D.fxc + rowo, pb, &bar);
+        tma_load_1d(sP, D.P + rowo, pb, &bar);
+        if (D.kahan) tma_load_1d(scP, D.cP + rowo, pb, &bar);
+        tma_load_1d(sw, wrow, pb, &bar);
+        if (seq) {
+            const T *Qr = D.Q + rowo - hx, *br = D.bC + rowo - hx;
+            tma_load_1d(sH + 0 * hspan, Qr, hb, &bar);
+            tma_load_1d(sH + 1 * hspan, Qr - D.pitch, hb, &bar);
+            tma_load_1d(sH + 2 * hspan, Qr + D.pitch, hb, &bar);
+            tma_load_1d(sH + 3 * hspan, br, hb, &bar);
+            tma_load_1d(sH + 4 * hspan, br - D.pitch, hb, &bar);
+            tma_load_1d(sH + 5 * hspan, br + D.pitch, hb, &bar);
+        }
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, 1LL << 24);
+    if (__syncthreads_or(!ok)) {
+        // copies did not complete: flag it, wait once more (bounded) so no
+        // copy still targets this block's shared memory, and give up; the
+        // controller of the next step sees the flag and stops the run
+        mbar_wait_bounded(&bar, 0, 1LL << 24);
+        if (t == 0) {
+            atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
+            next_step_controller(D, 0.0);
+        }
+        return;
+    }
+    if (seq) {
+        // Q^{n+1} ghosts at t_{n+1} where the staged rows need them: columns -1
+        // and nx of rows j-1, j, j+1 (W/E rule), then the whole ghost row when
+        // row j-1 or j+1 lies outside (S/N rule, applied to the filled row)
+        T *qrow[3] = {sH + 1 * hspan + hx, sH + 0 * hspan + hx, sH + 2 * hspan + hx};
+        if (t < 3) {
+            const int rr = j - 1 + t;
+            if (rr >= 0 && rr < D.ny) {
+                T *row = qrow[t];
+                row[-1] = D.bc[SW] == MAKER ? D.mqW[rr] : row[0];
+                row[nx] = D.bc[SE] == MAKER ? D.mqE[rr] : row[nx - 1];
+            }
+        }
+        __syncthreads();
+        if (j == 0 || j == D.ny - 1) {
+            const int side = j == 0 ? SS : SN;
+            const int gr = j == 0 ? -1 : D.ny;
+            T *dst = j == 0 ? qrow[0] : qrow[2];
+            const T *src = qrow[1];
+            const T *mq = side == SS ? D.mqS : D.mqN;  // maker Q at t_{n+1}, columns -1..nx
+            for (int c = t - 1; c <= nx; c += blockDim.x) dst[c] = D.bc[side] == MAKER ? mq[c + 1] : -src[c];
+            (void)gr;
+        }
+        __syncthreads();
+    }
+    if (!seq) {
+        // Q and bC of row j are still needed by the epilogue
+        const T *Qr = D.Q + rowo, *br = D.bC + rowo;
+        for (int q = t; q < span; q += blockDim.x) {
+            sH[0 * hspan + hx + q] = Qr[q];
+            sH[3 * hspan + hx + q] = br[q];
+        }
+        __syncthreads();
+    }
+    const int ib = t * K;
+    T r[K], m[K], e[K];
+#pragma unroll
+    for (int q = 0; q < K; q += VecT<T>::N) {
+        vload(sdU + ib + q, r + q);
+        vload(sm + ib + q, m + q);
+        vload(se + ib + q, e + q);
+    }
+    // row j of Q and bC (with one neighbour each side) stay in registers for
+    // the epilogue; all shared-memory reads are 16-byte vectors
+    T Qc[K + 2], bc_[K + 2];
+    load_halo_chunk<T, K>(sH + 0 * hspan + hx, ib, lane, Qc);
+    load_halo_chunk<T, K>(sH + 3 * hspan + hx, ib, lane, bc_);
+    if (seq) {
+        const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+        const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+        T qm[K + 2], qp[K + 2], bm[K], bp[K];
+        load_halo_chunk<T, K>(sH + 1 * hspan + hx, ib, lane, qm);
+        load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
+        vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
+        vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            T d = tmax(D.w_s - bc_[q + 1], (T)0);
+            T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
+            T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
+            T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
+            T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+            T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+            r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+        }
+    }
+    const T corrW = D.corrW[j], corrE = D.corrE[j];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        int i = ib + q;
+        if (i == 0) r[q] += corrW;
+        if (i == nx - 1) r[q] += corrE;
+        if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
+    }
+    T A = (T)1, B = (T)0;
+#pragma unroll
+    for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T Ap = __shfl_up_sync(0xffffffffu, A, o);
+        T Bp = __shfl_up_sync(0xffffffffu, B, o);
+        if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+    }
+    if (lane == 31) { sA[wid] = A; sB[wid] = B; }
+    T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) { Ae = (T)1; Be = (T)0; }
+    __syncthreads();
+    if (wid == 0) {
+        T a = lane < nw ? sA[lane] : (T)1, b = lane < nw ? sB[lane] : (T)0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_up_sync(0xffffffffu, a, o);
+            T bp = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { b = a * bp + b; a = a * ap; }
+        }
+        T bx = __shfl_up_sync(0xffffffffu, b, 1);
+        if (lane == 0) bx = (T)0;
+        if (lane < nw) sB[lane] = bx;
+    }
+    __syncthreads();
+    T y = Ae * sB[wid] + Be;
+#pragma unroll
+    for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
+    __syncthreads();
+    T c[K];
+#pragma unroll
+    for (int q = 0; q < K; q += VecT<T>::N) vload(sc + ib + q, c + q);
+#pragma unroll
+    for (int q = 0; q < K; q++)
+        if (ib + q >= nx) c[q] = (T)0;
+    T al = (T)0, be = (T)1;
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T ap = __shfl_down_sync(0xffffffffu, al, o);
+        T bp = __shfl_down_sync(0xffffffffu, be, o);
+        if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+    }
+    if (lane == 0) { sA[wid] = al; sB[wid] = be; }
+    T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
+    if (lane == 31) { an = (T)0; bn = (T)1; }
+    __syncthreads();
+    if (wid == 0) {
+        T a = lane < nw ? sA[lane] : (T)0, b = lane < nw ? sB[lane] : (T)1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, a, o);
+            T bp = __shfl_down_sync(0xffffffffu, b, o);
+            if (lane + o < 32) { a = a + b * ap; b = b * bp; }
+        }
+        T ax = __shfl_down_sync(0xffffffffu, a, 1);
+        if (lane == 31) ax = (T)0;
+        if (lane < nw) sA[lane] = ax;
+    }
+    __syncthreads();
+    T x = an + bn * sA[wid];
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
+
+    T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo;
+    T Pv[K], cPv[K], wv[K];
+    const T *Qv = Qc + 1, *bv = bc_ + 1;
+#pragma unroll
+    for (int q = 0; q < K; q += VecT<T>::N) {
+        vload(sP + ib + q, Pv + q);
+        if (D.kahan) vload(scP + ib + q, cPv + q);
+        vload(sw + ib + q, wv + q);
+    }
+    const T gyj = D.gy[j];
+    T rate = (T)0;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const int i = ib + q;
+        if (i >= nx) continue;
+        T Pn, cn = (T)0;
+        if (D.kahan) {
+            T yy = r[q] - cPv[q];
+            Pn = Pv[q] + yy;
+            cn = (Pn - Pv[q]) - yy;
+        } else {
+            Pn = Pv[q] + r[q];
+        }
+        T wq = wv[q];
+        T gm = D.gx[i] * gyj;
+        if (gm < (T)1) {
+            T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
+            wq = bv[q] + (d + gm * (h - d));
+            wrow[i] = wq;
+            if (D.kahan) cwr[i] = (T)0;
+            Pn *= gm;
+            cn *= gm;
+        }
+        Pv[q] = Pn;
+        cPv[q] = cn;
+        T h = tmax(wq - bv[q], (T)0);
+        T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
+        T u = iv * Pn, v = iv * Qv[q];
+        T cc = tsqrt(D.g * h);
+        rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+        if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+    }
+    vstore_k<T, K>(Pr + ib, Pv);
+    if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+    double rr = (double)rate;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    bool anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
+    __syncthreads();
+    if (t == 0) {
+        double mx = 0.0;
+        bool fl = false;
+        for (int q = 0; q < nw; q++) {
+            if (smax[q] < 0.0) fl = true;
+            else mx = fmax(mx, smax[q]);
+        }
+        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
+        atomicMax(&D.ctl->rate_bits, dbits(mx));
+        next_step_controller(D, forced_dt_next);
+    }
+}
+
+// shared memory bytes of the TMA x-solver for a row span
+template <typename T>
+static size_t xtma_smem(int span, int hx)
+{
+    return ((size_t)XT_ARR_PLAIN * span + (size_t)XT_ARR_HALO * (span + 2 * hx)) * sizeof(T);
 }
 
 // ------------------------------------------------------------------ utilities
@@ -982,86 +1677,122 @@ __global__ void k_set_limits(Ctl *ctl, double t_end, long long max_steps)
 
 // ------------------------------------------------------------------ launchers
 
+// y-solver shape: chunk length kch, chunks per column NCH, columns per block CW
 template <typename T>
-static void ysolve_shape(int nx, int ny, int &CW, int &NCH, int &kch)
+static void ysolve_shape(const Dev<T> &D, int &CW, int &NCH, int &kch)
 {
-    kch = sizeof(T) == 4 ? 32 : 16;
-    NCH = (ny + kch - 1) / kch;
+    kch = D.tune_ykch > 0 ? D.tune_ykch : (sizeof(T) == 4 ? 16 : 8);
+    NCH = (D.ny + kch - 1) / kch;
+    int maxthr = D.tune_ythreads > 0 ? min(D.tune_ythreads, 512) : 512;
     CW = 32;
-    while (CW > 1 && CW * NCH > 512) CW >>= 1;
-    (void)nx;
+    while (CW > 1 && CW * NCH > maxthr) CW >>= 1;
 }
 
 template <typename T>
 int step_shape_ok(int nx, int ny)
 {
-    int CW, NCH, kch;
-    ysolve_shape<T>(nx, ny, CW, NCH, kch);
-    return CW * NCH <= 1024;
+    // y-solver: at most 1024 chunks of 32 rows; x-solver: at most 512 threads of 32
+    return (ny + 31) / 32 <= 1024 && nx <= 512 * 32;
 }
 
+// x-solver chunk: elements per thread (a multiple of the vector width)
 template <typename T>
-static int xsolve_rows(int nseg)
+int x_chunk(int nx)
 {
-    size_t per = (size_t)nseg * 32 * VecT<T>::N * sizeof(T);
-    int rows = 4;
-    while (rows > 1 && rows * per > 96 * 1024) rows >>= 1;
-    return rows;
+    // at most 512 threads per row
+    int K = sizeof(T) == 4 ? 8 : 4;
+    while (K < 32 && (nx + K - 1) / K > 512) K *= 2;
+    return K;
 }
 
 template <typename T>
-size_t xsolve_smem(int nx)
+int row_pitch(int nx)
 {
-    constexpr int SEG = 32 * VecT<T>::N;
-    int nseg = (nx + SEG - 1) / SEG;
-    return (size_t)xsolve_rows<T>(nseg) * nseg * SEG * sizeof(T);
+    int span = 32 * x_chunk<T>(nx);
+    return ((nx + span - 1) / span) * span + span;
 }
 
-template <typename T>
-int row_segment() { return 32 * VecT<T>::N; }
+constexpr size_t XTMA_MAX_SMEM = 200 * 1024;
 
 template <typename T>
 cudaError_t configure(int nx)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_xsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)xsolve_smem<T>(nx) + 1024);
+    (void)nx;
+    const int bytes = (int)XTMA_MAX_SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_xsolve_tma<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_tma<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_tma<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_tma<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
-// One step: five launches on stream st.  With ev != nullptr, events ev[0..5]
-// are recorded before each launch and after the last (kernel timing).
+// One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
+// cells of Q where the x-solver does not patch them itself), x-line solves
+// whose last block runs the controller of the next step with forced_dt_next
+// (> 0: replay that step size).  With ev != nullptr, events ev[0..5] are
+// recorded before each launch and after the last (kernel timing).
 template <typename T>
-static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev)
+static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_next, cudaEvent_t *ev)
 {
     const int nx = D.nx, ny = D.ny;
     long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
     int gb = (int)((nwork + 255) / 256);
     if (ev) cudaEventRecord(ev[0], st);
-    k_ctl_ghost<T><<<gb, 256, 0, st>>>(D, forced_dt);
+    k_ghost<T><<<gb, 256, 0, st>>>(D);
     if (ev) cudaEventRecord(ev[1], st);
-    constexpr int TX = 32, TY = 8;
-    dim3 g1((nx + TX - 1) / TX, (ny + TY - 1) / TY);
-    k_rhs_combine<T, TX, TY><<<g1, dim3(TX, TY), 0, st>>>(D);
+    if (D.tune_rhs == 1) {
+        constexpr int TX = 32, TY = 8;
+        dim3 g1((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+        k_rhs_combine<T, TX, TY><<<g1, dim3(TX, TY), 0, st>>>(D);
+    } else {
+        const int rows = D.tune_rows > 0 ? D.tune_rows : 32;
+        const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
+        const int nband = (ny + rows - 1) / rows;
+        const long long nwarp = (long long)nstrip * nband;
+        const int blocks = (int)((nwarp + 3) / 4);
+        if (rows == 16) k_rhs_sw<T, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+        else if (rows == 64) k_rhs_sw<T, 64><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw<T, 32><<<blocks, 128, 0, st>>>(D, nstrip);
+    }
     if (ev) cudaEventRecord(ev[2], st);
     int CW, NCH, kch;
-    ysolve_shape<T>(nx, ny, CW, NCH, kch);
+    ysolve_shape<T>(D, CW, NCH, kch);
     size_t sm = 2 * (size_t)CW * NCH * sizeof(T);
-    if (kch == 32)
-        k_ysolve<T, 32><<<(nx + CW - 1) / CW, CW * NCH, sm, st>>>(D, CW, NCH);
-    else
-        k_ysolve<T, 16><<<(nx + CW - 1) / CW, CW * NCH, sm, st>>>(D, CW, NCH);
+    dim3 gy((nx + CW - 1) / CW);
+    if (kch == 32) k_ysolve<T, 32><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+    else if (kch == 8) k_ysolve<T, 8><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+    else k_ysolve<T, 16><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
     if (ev) cudaEventRecord(ev[3], st);
-    if (D.cross_mode != 0) {
+    const int K = x_chunk<T>(nx);
+    int thr = ((nx + K - 1) / K + 31) / 32 * 32;
+    const int span = thr * K;
+    const size_t xs = xtma_smem<T>(span, D.hx);
+    const bool tma = D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM;
+    if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    constexpr int SEG = 32 * VecT<T>::N;
-    int nseg = (nx + SEG - 1) / SEG;
-    int rows = xsolve_rows<T>(nseg);
-    size_t smx = (size_t)rows * nseg * SEG * sizeof(T);
-    k_xsolve<T><<<(ny + rows - 1) / rows, dim3(32, rows), smx, st>>>(D, nseg);
+    if (tma) {
+        if (K == 4) k_xsolve_tma<T, 4><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
+        else if (K == 8) k_xsolve_tma<T, 8><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
+        else if (K == 16) k_xsolve_tma<T, 16><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
+        else k_xsolve_tma<T, 32><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
+    } else if (K == 4) k_xsolve<T, 4><<<ny, thr, 0, st>>>(D, forced_dt_next);
+    else if (K == 8) k_xsolve<T, 8><<<ny, thr, 0, st>>>(D, forced_dt_next);
+    else if (K == 16) k_xsolve<T, 16><<<ny, thr, 0, st>>>(D, forced_dt_next);
+    else k_xsolve<T, 32><<<ny, thr, 0, st>>>(D, forced_dt_next);
     if (ev) cudaEventRecord(ev[5], st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt)
+{
+    k_prologue<T><<<1, 1, 0, st>>>(D, forced_dt);
     return cudaGetLastError();
 }
 
@@ -1110,12 +1841,12 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
 
 #define BSQ_INST(T)                                                                              \
     template int step_shape_ok<T>(int, int);                                                     \
-    template size_t xsolve_smem<T>(int);                                                         \
-    template int row_segment<T>();                                                               \
+    template int row_pitch<T>(int);                                                              \
     template cudaError_t configure<T>(int);                                                      \
     template cudaError_t launch_step<T>(const Dev<T> &, cudaStream_t, double);                   \
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
+    template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
     template cudaError_t launch_extract<T>(const Dev<T> &, cudaStream_t, int, int, T *);         \
     template cudaError_t launch_mass<T>(const Dev<T> &, cudaStream_t, int, double *, int);
 BSQ_INST(float)

@@ -10,11 +10,11 @@
 namespace bsq {
 
 template <typename T> int step_shape_ok(int nx, int ny);
-template <typename T> size_t xsolve_smem(int nx);
-template <typename T> int row_segment();
+template <typename T> int row_pitch(int nx);
 template <typename T> cudaError_t configure(int nx);
 template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
+template <typename T> cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, int wc);
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
 template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);

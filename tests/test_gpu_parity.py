@@ -219,3 +219,19 @@ def test_bounded_wait_times_out():
         with pytest.raises(bsq.BsqError) as ei:
             d.advance(max_steps=2000)
         assert ei.value.status == bsq.ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("tune", [(0, 0, 1, 0), (0, 0, 2, 0), (0, 0, 3, 0), (8, 256, 0, 16), (32, 512, 0, 64)])
+def test_kernel_variants_match_oracle(tune):
+    # every kernel shape (tiled or sliding-window RHS, TMA-staged or register
+    # x-solver, y-solver chunk sizes) gives the same step to FP64 round-off
+    case = CASES["barred_beach_rips"]()
+    o = _oracle(case)
+    dts = o.run(80)
+    with bsq.Domain(case, precision="fp64", tune=tune) as d:
+        d.step_dt(dts)
+        for f in ("eta", "P", "Q"):
+            assert rel(d.read(f), o.get(f)) <= FP64_TOL, (tune, f)
+    with bsq.Domain(case, precision="fp32", tune=tune) as d:
+        d.step_dt(dts)
+        assert rel(d.read("eta"), o.get("eta")) <= FP32_TOL, tune
