@@ -310,6 +310,8 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     size_t o_ctl = take(sizeof(Ctl)), o_coef = take(sizeof(Coef));
     dm->mass_blocks = 512;
     size_t o_mass = take(dm->mass_blocks * sizeof(double));
+    const size_t nchy = (size_t)ysplit_chunks<T>(ny) * nx;
+    size_t o_ysum = take(7 * nchy * sizeof(T));
     dm->dbytes = off;
     if (cudaMalloc(&dm->dmem, off) != cudaSuccess) { dm->dmem = nullptr; return BSQ_ERR_OOM; }
     char *base = (char *)dm->dmem;
@@ -329,6 +331,13 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_xtma = (p.tune[2] & 2) ? 1 : 0;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            return BSQ_ERR_CUDA;
+        D.nsm = nsm;
+    }
     for (int s = 0; s < 4; s++) D.bc[s] = bt[s];
     D.cfl = p.cfl; D.ema_alpha = p.ema_alpha; D.dt_init = p.dt_init; D.dt_min = p.dt_min;
     D.dt_max = p.dt_max; D.ramp_time = p.ramp_time;
@@ -362,6 +371,11 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     dm->ctl = D.ctl;
     dm->coef = D.coef;
     dm->mass_partial = (double *)(base + o_mass);
+    // explicit y-solver shapes, or columns of more than 256 chunks, select the block-scan kernel
+    D.ysplit = (p.tune[0] == 0 && p.tune[1] == 0 && ysplit_chunks<T>(ny) <= 256) ? 1 : 0;
+    D.ysums = (T *)(base + o_ysum);
+    D.yin = D.ysums + 5 * nchy;
+    D.yxa = D.ysums + 6 * nchy;
     dm->n_state_fields = nstate + 15;
 
     // uploads (synchronous copies from pageable memory, then a stream sync)

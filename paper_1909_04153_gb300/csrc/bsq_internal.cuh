@@ -56,6 +56,9 @@ struct Dev {
     int tune_ykch, tune_ythreads;  // y-solver chunk rows and block size (0: default)
     int tune_rhs, tune_rows;       // RHS kernel variant (0 sliding window, 1 tiled), rows per warp
     int tune_xtma;                 // 0: TMA-staged x-solver when it fits, 1: register version
+    int nsm;                       // multiprocessors of the device
+    int ysplit;                    // 1: three-launch y-solver (summaries, scans, apply)
+    T *ysums, *yin, *yxa;          // its chunk summaries (5 per chunk) and scanned values
     int bc[4];
     // controller inputs (FP64)
     double cfl, ema_alpha, dt_init, dt_min, dt_max;

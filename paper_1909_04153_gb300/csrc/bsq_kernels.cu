@@ -1021,6 +1021,188 @@ __global__ void __launch_bounds__(512, 2) k_ysolve(Dev<T> D, int CW, int NCH)
     }
 }
 
+// ------------------------------------------------------------------ y-line solves, split
+
+// Three launches instead of one block scan: (A) every (column, chunk of KY
+// rows) summarises its chunk -- the forward elimination y_j = m_j r_j + e_j y_{j-1}
+// as y_end = A y_in + B, and the back substitution x_j = y_j - c'_j x_{j+1} as
+// x_first = al0 + al1 y_in + be x_after (y is affine in y_in); (B) one warp per
+// column scans the summaries (forward, then backward); (C) every chunk
+// recomputes its y from y_in, substitutes back from x_after, and updates Q.
+// No thread waits on another inside a kernel; all accesses are coalesced
+// across 32 columns.
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_ysum(Dev<T> D, int nch, T *sums)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = D.nx, ny = D.ny;
+    if (i >= nx || k >= nch) return;
+    const int j0 = k * KY;
+    T yt = (T)0, Pi = (T)1, al0 = (T)0, al1 = (T)0, be = (T)1;
+    T rr[KY], mm[KY], ee[KY], cc[KY];
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        const int j = j0 + q;
+        const bool v = j < ny;
+        const long long o = v ? fidx(D, i, j) : 0;
+        T r = v ? D.dV[o] : (T)0;
+        if (j == 0) r += D.corrS[i];
+        if (j == ny - 1) r += D.corrN[i];
+        rr[q] = r;
+        mm[q] = v ? D.fym[o] : (T)0;
+        ee[q] = v ? D.fye[o] : (T)1;
+        cc[q] = v ? D.fyc[o] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        yt = mm[q] * rr[q] + ee[q] * yt;
+        Pi = ee[q] * Pi;
+        al0 = al0 + be * yt;
+        al1 = al1 + be * Pi;
+        be = -cc[q] * be;
+    }
+    const long long s = (long long)nx * nch, o = (long long)i * nch + k;
+    sums[o] = Pi;            // A
+    sums[s + o] = yt;        // B
+    sums[2 * s + o] = al0;
+    sums[3 * s + o] = al1;
+    sums[4 * s + o] = be;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums, T *yin, T *xaft)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nx = D.nx;
+    if (i >= nx) return;
+    const long long s = (long long)nx * nch, base = (long long)i * nch;
+    constexpr int CPL = 8;  // chunks per lane (nch <= 256)
+    // forward: lane composes its chunks, warp scan, exclusive values per chunk
+    T A = (T)1, B = (T)0;
+    T a_[CPL], b_[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        const int k = lane * CPL + q;
+        a_[q] = k < nch ? sums[base + k] : (T)1;
+        b_[q] = k < nch ? sums[s + base + k] : (T)0;
+        B = a_[q] * B + b_[q];
+        A = a_[q] * A;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+        if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+    }
+    T y = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) y = (T)0;
+    T yk[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        yk[q] = y;
+        y = a_[q] * y + b_[q];
+    }
+    // backward: x_first(k) = (al0 + al1 y_in(k)) + be x_after(k)
+    T al = (T)0, bb = (T)1;
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        const int k = lane * CPL + q;
+        a_[q] = k < nch ? sums[2 * s + base + k] + sums[3 * s + base + k] * yk[q] : (T)0;
+        b_[q] = k < nch ? sums[4 * s + base + k] : (T)1;
+    }
+#pragma unroll
+    for (int q = CPL - 1; q >= 0; q--) { al = a_[q] + b_[q] * al; bb = b_[q] * bb; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T ap = __shfl_down_sync(0xffffffffu, al, o), bp = __shfl_down_sync(0xffffffffu, bb, o);
+        if (lane + o < 32) { al = al + bb * ap; bb = bb * bp; }
+    }
+    T x = __shfl_down_sync(0xffffffffu, al, 1);
+    if (lane == 31) x = (T)0;
+#pragma unroll
+    for (int q = CPL - 1; q >= 0; q--) {
+        const int k = lane * CPL + q;
+        if (k < nch) {
+            yin[base + k] = yk[q];
+            xaft[base + k] = x;
+        }
+        x = a_[q] + b_[q] * x;
+    }
+}
+
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = D.nx, ny = D.ny;
+    if (i >= nx || k >= nch) return;
+    const int j0 = k * KY;
+    const long long bo = (long long)i * nch + k;
+    // all loads of a phase are issued before any store, so they overlap
+    T rr[KY], mm[KY], ee[KY];
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        const int j = j0 + q;
+        const bool v = j < ny;
+        const long long o = v ? fidx(D, i, j) : 0;
+        T r = v ? D.dV[o] : (T)0;
+        if (j == 0) r += D.corrS[i];
+        if (j == ny - 1) r += D.corrN[i];
+        rr[q] = r;
+        mm[q] = v ? D.fym[o] : (T)0;
+        ee[q] = v ? D.fye[o] : (T)1;
+    }
+    T y = yin[bo];
+#pragma unroll
+    for (int q = 0; q < KY; q++) { y = mm[q] * rr[q] + ee[q] * y; rr[q] = y; }
+    T cc[KY], Qo[KY], cq[KY];
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        const int j = j0 + q;
+        const bool v = j < ny;
+        const long long o = v ? fidx(D, i, j) : 0;
+        cc[q] = v ? D.fyc[o] : (T)0;
+        Qo[q] = v ? D.Q[o] : (T)0;
+        cq[q] = (v && D.kahan) ? D.cQ[o] : (T)0;
+    }
+    T x = xaft[bo];
+    const T gxi = D.gx[i];
+#pragma unroll
+    for (int q = KY - 1; q >= 0; q--) {
+        x = rr[q] - cc[q] * x;
+        T Qn, cn = (T)0;
+        if (D.kahan) {
+            T yy = x - cq[q];
+            Qn = Qo[q] + yy;
+            cn = (Qn - Qo[q]) - yy;
+        } else {
+            Qn = Qo[q] + x;
+        }
+        const int j = j0 + q;
+        T gm = gxi * D.gy[min(j, ny - 1)];
+        if (gm < (T)1) { Qn *= gm; cn *= gm; }
+        Qo[q] = Qn;
+        cq[q] = cn;
+    }
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        const int j = j0 + q;
+        if (j < ny) {
+            const long long o = fidx(D, i, j);
+            D.Q[o] = Qo[q];
+            if (D.kahan) D.cQ[o] = cq[q];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ x-line solves
 
 template <typename T> struct VecT;
@@ -1585,6 +1767,275 @@ __global__ void __launch_bounds__(512) k_xsolve_tma(Dev<T> D, int span, double f
     }
 }
 
+// Issue the bulk copies of row j into one staging buffer (thread 0).
+template <typename T>
+__device__ __forceinline__ void xrow_issue(const Dev<T> &D, const Coef &cf, int j, T *S, int span,
+                                           unsigned long long *bar)
+{
+    const int hx = D.hx, hspan = span + 2 * hx;
+    const long long rowo = fidx(D, 0, j);
+    const bool seq = D.cross_mode != 0;
+    const unsigned pb = (unsigned)(span * sizeof(T)), hb = (unsigned)(hspan * sizeof(T));
+    unsigned total = 6u * pb + (D.kahan ? pb : 0u) + 2u * hb + (seq ? 4u * hb : 0u);
+    mbar_expect_tx(bar, total);
+    tma_load_1d(S + 0 * span, D.dU + rowo, pb, bar);
+    tma_load_1d(S + 1 * span, D.fxm + rowo, pb, bar);
+    tma_load_1d(S + 2 * span, D.fxe + rowo, pb, bar);
+    tma_load_1d(S + 3 * span, D.fxc + rowo, pb, bar);
+    tma_load_1d(S + 4 * span, D.P + rowo, pb, bar);
+    if (D.kahan) tma_load_1d(S + 5 * span, D.cP + rowo, pb, bar);
+    tma_load_1d(S + 6 * span, D.w[cf.wc ^ 1] + rowo, pb, bar);
+    T *sH = S + 7 * span;
+    const T *Qr = D.Q + rowo - hx, *br = D.bC + rowo - hx;
+    tma_load_1d(sH + 0 * hspan, Qr, hb, bar);
+    tma_load_1d(sH + 3 * hspan, br, hb, bar);
+    if (seq) {
+        tma_load_1d(sH + 1 * hspan, Qr - D.pitch, hb, bar);
+        tma_load_1d(sH + 2 * hspan, Qr + D.pitch, hb, bar);
+        tma_load_1d(sH + 4 * hspan, br - D.pitch, hb, bar);
+        tma_load_1d(sH + 5 * hspan, br + D.pitch, hb, bar);
+    }
+}
+
+// Persistent x-line solver: one block per SM walks rows blockIdx.x,
+// blockIdx.x + gridDim.x, ...; two staging buffers, so the bulk copies of the
+// next row are in flight while the current row is solved (same arithmetic as
+// k_xsolve).
+template <typename T, int K>
+__global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, double forced_dt_next)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ T sA[32], sB[32];
+    __shared__ double smax[32];
+    const int hx = D.hx;
+    const int hspan = span + 2 * hx;
+    const size_t per = (size_t)7 * span + (size_t)6 * hspan;
+    T *buf0 = reinterpret_cast<T *>(smem_raw), *buf1 = buf0 + per;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int nx = D.nx, ny = D.ny;
+    const bool seq = D.cross_mode != 0;
+    const int ib = t * K;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+        if ((int)blockIdx.x < ny) xrow_issue(D, cf, blockIdx.x, buf0, span, &bar[0]);
+    }
+    __syncthreads();
+    T rate = (T)0;
+    bool bad = false, failed = false;
+    int it = 0;
+    for (int j = blockIdx.x; j < ny; j += gridDim.x, it++) {
+        T *S = (it & 1) ? buf1 : buf0;
+        unsigned long long *b = &bar[it & 1];
+        const bool ok = mbar_wait_bounded(b, (unsigned)((it >> 1) & 1), 1LL << 24);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        // the other buffer was released by the barrier that ended the last row;
+        // order those shared-memory reads before the bulk copies overwrite it
+        if (t == 0 && j + (int)gridDim.x < ny) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            xrow_issue(D, cf, j + gridDim.x, (it & 1) ? buf0 : buf1, span, &bar[(it + 1) & 1]);
+        }
+        const long long rowo = fidx(D, 0, j);
+        T *sdU = S, *sm = S + span, *se = S + 2 * span, *sc = S + 3 * span, *sP = S + 4 * span;
+        T *scP = S + 5 * span, *sw = S + 6 * span, *sH = S + 7 * span;
+        if (seq) {
+            T *qrow[3] = {sH + 1 * hspan + hx, sH + 0 * hspan + hx, sH + 2 * hspan + hx};
+            if (t < 3) {
+                const int rr = j - 1 + t;
+                if (rr >= 0 && rr < ny) {
+                    T *row = qrow[t];
+                    row[-1] = D.bc[SW] == MAKER ? D.mqW[rr] : row[0];
+                    row[nx] = D.bc[SE] == MAKER ? D.mqE[rr] : row[nx - 1];
+                }
+            }
+            __syncthreads();
+            if (j == 0 || j == ny - 1) {
+                const int side = j == 0 ? SS : SN;
+                T *dst = j == 0 ? qrow[0] : qrow[2];
+                const T *src = qrow[1];
+                const T *mq = side == SS ? D.mqS : D.mqN;
+                for (int c = t - 1; c <= nx; c += blockDim.x) dst[c] = D.bc[side] == MAKER ? mq[c + 1] : -src[c];
+            }
+            __syncthreads();
+        }
+        T r[K], m[K], e[K];
+        vload_k<T, K>(sdU + ib, r);
+        vload_k<T, K>(sm + ib, m);
+        vload_k<T, K>(se + ib, e);
+        T Qc[K + 2], bc_[K + 2];
+        load_halo_chunk<T, K>(sH + 0 * hspan + hx, ib, lane, Qc);
+        load_halo_chunk<T, K>(sH + 3 * hspan + hx, ib, lane, bc_);
+        if (seq) {
+            const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+            const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+            T qm[K + 2], qp[K + 2], bm[K], bp[K];
+            load_halo_chunk<T, K>(sH + 1 * hspan + hx, ib, lane, qm);
+            load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
+            vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
+            vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                T d = tmax(D.w_s - bc_[q + 1], (T)0);
+                T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
+                T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
+                T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
+                T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+                T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+            }
+        }
+        const T corrW = D.corrW[j], corrE = D.corrE[j];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            int i = ib + q;
+            if (i == 0) r[q] += corrW;
+            if (i == nx - 1) r[q] += corrE;
+            if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
+        }
+        T A = (T)1, B = (T)0;
+#pragma unroll
+        for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T Ap = __shfl_up_sync(0xffffffffu, A, o);
+            T Bp = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+        }
+        if (lane == 31) { sA[wid] = A; sB[wid] = B; }
+        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) { Ae = (T)1; Be = (T)0; }
+        __syncthreads();
+        if (wid == 0) {
+            T a = lane < nw ? sA[lane] : (T)1, bb = lane < nw ? sB[lane] : (T)0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                T ap = __shfl_up_sync(0xffffffffu, a, o);
+                T bp = __shfl_up_sync(0xffffffffu, bb, o);
+                if (lane >= o) { bb = a * bp + bb; a = a * ap; }
+            }
+            T bx = __shfl_up_sync(0xffffffffu, bb, 1);
+            if (lane == 0) bx = (T)0;
+            if (lane < nw) sB[lane] = bx;
+        }
+        __syncthreads();
+        T y = Ae * sB[wid] + Be;
+#pragma unroll
+        for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
+        __syncthreads();
+        T c[K];
+        vload_k<T, K>(sc + ib, c);
+#pragma unroll
+        for (int q = 0; q < K; q++)
+            if (ib + q >= nx) c[q] = (T)0;
+        T al = (T)0, be = (T)1;
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, al, o);
+            T bp = __shfl_down_sync(0xffffffffu, be, o);
+            if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+        }
+        if (lane == 0) { sA[wid] = al; sB[wid] = be; }
+        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
+        if (lane == 31) { an = (T)0; bn = (T)1; }
+        __syncthreads();
+        if (wid == 0) {
+            T a = lane < nw ? sA[lane] : (T)0, bb = lane < nw ? sB[lane] : (T)1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                T ap = __shfl_down_sync(0xffffffffu, a, o);
+                T bp = __shfl_down_sync(0xffffffffu, bb, o);
+                if (lane + o < 32) { a = a + bb * ap; bb = bb * bp; }
+            }
+            T ax = __shfl_down_sync(0xffffffffu, a, 1);
+            if (lane == 31) ax = (T)0;
+            if (lane < nw) sA[lane] = ax;
+        }
+        __syncthreads();
+        T x = an + bn * sA[wid];
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
+
+        T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo;
+        T *wrow = D.w[cf.wc ^ 1] + rowo;
+        T Pv[K], cPv[K], wv[K];
+        const T *Qv = Qc + 1, *bv = bc_ + 1;
+        vload_k<T, K>(sP + ib, Pv);
+        if (D.kahan) vload_k<T, K>(scP + ib, cPv);
+        vload_k<T, K>(sw + ib, wv);
+        const T gyj = D.gy[j];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const int i = ib + q;
+            if (i >= nx) continue;
+            T Pn, cn = (T)0;
+            if (D.kahan) {
+                T yy = r[q] - cPv[q];
+                Pn = Pv[q] + yy;
+                cn = (Pn - Pv[q]) - yy;
+            } else {
+                Pn = Pv[q] + r[q];
+            }
+            T wq = wv[q];
+            T gm = D.gx[i] * gyj;
+            if (gm < (T)1) {
+                T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
+                wq = bv[q] + (d + gm * (h - d));
+                wrow[i] = wq;
+                if (D.kahan) cwr[i] = (T)0;
+                Pn *= gm;
+                cn *= gm;
+            }
+            Pv[q] = Pn;
+            cPv[q] = cn;
+            T h = tmax(wq - bv[q], (T)0);
+            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
+            T u = iv * Pn, v = iv * Qv[q];
+            T cc = tsqrt(D.g * h);
+            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+        }
+        if (ib < nx) {
+            vstore_k<T, K>(Pr + ib, Pv);
+            if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+        }
+        __syncthreads();  // this buffer may be refilled from the next iteration on
+    }
+    if (failed) {
+        // copies did not complete: flag it, wait (bounded) for what is in
+        // flight, let the controller of the next step stop the run
+        mbar_wait_bounded(&bar[0], 0, 1LL << 22);
+        mbar_wait_bounded(&bar[1], 0, 1LL << 22);
+        if (t == 0) {
+            atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
+            next_step_controller(D, 0.0);
+        }
+        return;
+    }
+    double rr = (double)rate;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    bool anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
+    __syncthreads();
+    if (t == 0) {
+        double mx = 0.0;
+        bool fl = false;
+        for (int q = 0; q < nw; q++) {
+            if (smax[q] < 0.0) fl = true;
+            else mx = fmax(mx, smax[q]);
+        }
+        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
+        atomicMax(&D.ctl->rate_bits, dbits(mx));
+        next_step_controller(D, forced_dt_next);
+    }
+}
+
 // shared memory bytes of the TMA x-solver for a row span
 template <typename T>
 static size_t xtma_smem(int span, int hx)
@@ -1682,6 +2133,7 @@ template <typename T>
 static void ysolve_shape(const Dev<T> &D, int &CW, int &NCH, int &kch)
 {
     kch = D.tune_ykch > 0 ? D.tune_ykch : (sizeof(T) == 4 ? 16 : 8);
+    while (kch < 32 && (D.ny + kch - 1) / kch > 512) kch *= 2;
     NCH = (D.ny + kch - 1) / kch;
     int maxthr = D.tune_ythreads > 0 ? min(D.tune_ythreads, 512) : 512;
     CW = 32;
@@ -1689,10 +2141,18 @@ static void ysolve_shape(const Dev<T> &D, int &CW, int &NCH, int &kch)
 }
 
 template <typename T>
+int ysplit_chunks(int ny)
+{
+    const int KY = sizeof(T) == 4 ? 16 : 8;
+    return (ny + KY - 1) / KY;
+}
+
+template <typename T>
 int step_shape_ok(int nx, int ny)
 {
-    // y-solver: at most 1024 chunks of 32 rows; x-solver: at most 512 threads of 32
-    return (ny + 31) / 32 <= 1024 && nx <= 512 * 32;
+    // y-solver: block scan over at most 512 chunks of 32 rows (the split
+    // y-solver takes over up to 256 chunks); x-solver: at most 512 threads of 32
+    return (ny + 31) / 32 <= 512 && nx <= 512 * 32;
 }
 
 // x-solver chunk: elements per thread (a multiple of the vector width)
@@ -1713,6 +2173,7 @@ int row_pitch(int nx)
 }
 
 constexpr size_t XTMA_MAX_SMEM = 200 * 1024;
+constexpr size_t XPIPE_MAX_SMEM = 220 * 1024;
 
 template <typename T>
 cudaError_t configure(int nx)
@@ -1726,6 +2187,15 @@ cudaError_t configure(int nx)
         e = cudaFuncSetAttribute(k_xsolve_tma<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_tma<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int pb = (int)XPIPE_MAX_SMEM;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_pipe<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_pipe<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_pipe<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_pipe<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     return e;
 }
 
@@ -1758,25 +2228,41 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         else k_rhs_sw<T, 32><<<blocks, 128, 0, st>>>(D, nstrip);
     }
     if (ev) cudaEventRecord(ev[2], st);
-    int CW, NCH, kch;
-    ysolve_shape<T>(D, CW, NCH, kch);
-    size_t sm = 2 * (size_t)CW * NCH * sizeof(T);
-    dim3 gy((nx + CW - 1) / CW);
-    if (kch == 32) k_ysolve<T, 32><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
-    else if (kch == 8) k_ysolve<T, 8><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
-    else k_ysolve<T, 16><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+    if (D.ysplit) {
+        constexpr int KY = sizeof(T) == 4 ? 16 : 8;
+        const int nch = (ny + KY - 1) / KY;
+        dim3 gb2((nx + 31) / 32, (nch + 7) / 8);
+        k_ysum<T, KY><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+        k_yscan<T><<<(int)(((long long)nx * 32 + 255) / 256), 256, 0, st>>>(D, nch, D.ysums, D.yin, D.yxa);
+        k_yapply<T, KY><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
+    } else {
+        int CW, NCH, kch;
+        ysolve_shape<T>(D, CW, NCH, kch);
+        size_t sm = 2 * (size_t)CW * NCH * sizeof(T);
+        dim3 gy((nx + CW - 1) / CW);
+        if (kch == 32) k_ysolve<T, 32><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+        else if (kch == 8) k_ysolve<T, 8><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+        else k_ysolve<T, 16><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     const int K = x_chunk<T>(nx);
     int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
-    const bool tma = D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM;
+    const bool pipe = D.tune_xtma == 0 && 2 * xs <= XPIPE_MAX_SMEM;
+    const bool tma = pipe || (D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM);
     if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (tma) {
+    if (pipe) {
+        const int grid = min(ny, D.nsm);
+        if (K == 4) k_xsolve_pipe<T, 4><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
+        else if (K == 8) k_xsolve_pipe<T, 8><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
+        else if (K == 16) k_xsolve_pipe<T, 16><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
+        else k_xsolve_pipe<T, 32><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
+    } else if (tma) {
         if (K == 4) k_xsolve_tma<T, 4><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
         else if (K == 8) k_xsolve_tma<T, 8><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
         else if (K == 16) k_xsolve_tma<T, 16><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
@@ -1842,6 +2328,7 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
 #define BSQ_INST(T)                                                                              \
     template int step_shape_ok<T>(int, int);                                                     \
     template int row_pitch<T>(int);                                                              \
+    template int ysplit_chunks<T>(int);                                                          \
     template cudaError_t configure<T>(int);                                                      \
     template cudaError_t launch_step<T>(const Dev<T> &, cudaStream_t, double);                   \
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\
