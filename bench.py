@@ -36,7 +36,14 @@ import numpy as np  # noqa: E402
 from paper_1909_04153_gb300 import workloads as W  # noqa: E402
 
 METRIC = "cell-updates/s"
-N_KERNELS = 5
+# floating-point operations of one cell-update, counted from the FP32 step
+# kernels' instruction mix (add, mul, 2 x fma) without halo recomputation
+FLOPS_PER_CELL = 420
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is recorded)
+# DRAM bytes per launch of the dominant kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (kernel, precision, nx, ny); the capture is summarised under profiles/
+MEASURED_TRAFFIC = {}
 # algorithmic bytes per interior cell of each kernel (values it must read +
 # write once), per precision; the whole step in STEP_VALUES
 KERNEL_VALUES = {"fp32": {"rhs_combine": 21, "ysolve": 8, "xsolve": 11},
@@ -254,7 +261,31 @@ def run_ours(args):
     step_bytes = STEP_VALUES[fp] * esize
     step_achieved = value / world * step_bytes / 1e9
     info = dom.info()
+    launches = dom.launches_per_step()
     dom.close()
+    traffic = MEASURED_TRAFFIC.get((top, fp, p["nx"], p["ny"]))
+
+    # the FP64 path on the same workload (ALU bound on GB300), short run
+    fp64 = None
+    if prec == "fp32" and not args.no_fp64:
+        d64 = bsq.Domain(case, precision="fp64", stream=stream.cuda_stream, graph_steps=args.graph_steps)
+        d64.advance(max_steps=5)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        d64.advance(max_steps=args.fp64_steps)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        k64 = d64.profile_kernels(3)
+        d64.close()
+        v64 = ncell / (ms64 * 1e-3)
+        fl = FLOPS_PER_CELL * v64 / 1e12
+        fp64 = {"value": v64, "unit": "cell-updates/s", "ms_per_step": ms64, "steps": args.fp64_steps,
+                "kernel_ms": k64,
+                "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": fl / FP64_PEAK_TFLOPS, "peak_kind": "nominal",
+                             "flops_per_cell": FLOPS_PER_CELL}}
 
     # end to end through the C ABI with host buffers: create (uploads the
     # bathymetry and initial state), advance, read eta back
@@ -293,13 +324,15 @@ def run_ours(args):
                            bsq_bytes_estimate(ncell, fp) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": None, "bytes_per_cell": KERNEL_VALUES[fp][top] * esize},
+                         "traffic": traffic, "bytes_per_cell": KERNEL_VALUES[fp][top] * esize},
             "step_roofline": {"bytes_per_cell_update": step_bytes, "achieved": step_achieved,
                               "frac": step_achieved / peak, "peak": peak},
             "kernel_ms": kms,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": N_KERNELS * args.graph_steps * math.ceil(args.steps / args.graph_steps) + 1,
+            "gpu_launches": launches * args.graph_steps * math.ceil(args.steps / args.graph_steps) + 2,
+            "launches_per_step": launches,
+            "fp64": fp64,
             "clocks": clocks,
             "sim": {"t": info["t"], "clamps": info["clamps"]},
         }
@@ -326,6 +359,8 @@ def main(argv=None):
     ap.add_argument("--graph-steps", type=int, default=16)
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=40)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -173,6 +173,10 @@ size_t bsq_device_bytes(const bsq_domain *d);
 bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels);
 const char *bsq_kernel_name(int k);
 
+/* Kernel launches one step makes (each a node of the captured graphs);
+ * 0 for a NULL handle. */
+int bsq_launches_per_step(const bsq_domain *d);
+
 /* Allocation-free variant of the volume reduction that bsq_info's mass uses.
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc, such as an application that owns every byte of device memory

@@ -91,6 +91,8 @@ def lib():
         L.bsq_profile_kernels.argtypes = [vp, ctypes.c_longlong, _DP, ctypes.POINTER(ctypes.c_int)]
         L.bsq_kernel_name.restype = ctypes.c_char_p
         L.bsq_kernel_name.argtypes = [ctypes.c_int]
+        L.bsq_launches_per_step.restype = ctypes.c_int
+        L.bsq_launches_per_step.argtypes = [vp]
         L.bsq_mass_noalloc.restype = ctypes.c_int
         L.bsq_mass_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                        ctypes.c_double, ctypes.c_double, vp, vp]
@@ -313,3 +315,6 @@ class Domain:
 
     def profile_kernels(self, n_steps: int) -> dict:
         return bsq_profile_kernels(self.h, n_steps)
+
+    def launches_per_step(self) -> int:
+        return lib().bsq_launches_per_step(self.h)

@@ -802,3 +802,15 @@ extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, doub
     }
     return set_sticky(d, st);
 }
+
+extern "C" int bsq_launches_per_step(const bsq_domain *d)
+{
+    if (!d) return 0;
+    const int ysplit = d->fp64 ? d->Dd.ysplit : d->Df.ysplit;
+    const int nx = d->nx;
+    int tma;
+    if (d->fp64) tma = xsolver_staged<double>(d->Dd, nx);
+    else tma = xsolver_staged<float>(d->Df, nx);
+    const int cross = d->p.cross_mode != 0;
+    return 1 /* ghost */ + 1 /* rhs */ + (ysplit ? 3 : 1) + ((cross && !tma) ? 1 : 0) + 1 /* x-solver */;
+}

@@ -690,7 +690,7 @@ constexpr int SW_COLS = 28;  // interior columns per warp strip (lanes 2..29)
 // x-reconstruction and x-face flux (neighbours by shuffles), bed source,
 // friction, dispersive differences (Eqs. 12-15) and the AB3 combine.  Every
 // reconstruction and every face flux is computed once per strip.
-template <typename T, int ROWS>
+template <typename T, int ROWS, bool THETA1>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
 {
     const Coef cf = *D.coef;
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
     const int kc = min(i, nx + 2), kc1 = min(i + 1, nx + 2);
     const bool lane_out = lane >= 2 && lane <= 29 && i < nx;
     const T *w = D.w[cf.wc];
-    const T g = D.g, eps = D.eps, th = D.theta;
+    const T g = D.g, eps = D.eps, th = THETA1 ? (T)1 : D.theta;
     const T rdx = D.rdx, rdy = D.rdy, half_rdx = (T)0.5 * rdx, half_rdy = (T)0.5 * rdy;
     const T rdx2 = rdx * rdx, rdy2 = rdy * rdy, q_rdxy = (T)0.25 * rdx * rdy;
     const T c_xxx = (T)0.5 * rdx2 * rdx, c_yyy = (T)0.5 * rdy2 * rdy;
@@ -2223,9 +2223,17 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const int nband = (ny + rows - 1) / rows;
         const long long nwarp = (long long)nstrip * nband;
         const int blocks = (int)((nwarp + 3) / 4);
-        if (rows == 16) k_rhs_sw<T, 16><<<blocks, 128, 0, st>>>(D, nstrip);
-        else if (rows == 64) k_rhs_sw<T, 64><<<blocks, 128, 0, st>>>(D, nstrip);
-        else k_rhs_sw<T, 32><<<blocks, 128, 0, st>>>(D, nstrip);
+        const bool t1 = D.theta == (T)1;
+        if (rows == 16) {
+            if (t1) k_rhs_sw<T, 16, true><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 16, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        } else if (rows == 64) {
+            if (t1) k_rhs_sw<T, 64, true><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 64, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        } else {
+            if (t1) k_rhs_sw<T, 32, true><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 32, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        }
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (D.ysplit) {
@@ -2273,6 +2281,16 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     else k_xsolve<T, 32><<<ny, thr, 0, st>>>(D, forced_dt_next);
     if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
+}
+
+// 1 when the x-solver stages rows in shared memory (and patches Q ghosts there)
+template <typename T>
+int xsolver_staged(const Dev<T> &D, int nx)
+{
+    const int K = x_chunk<T>(nx);
+    const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
+    const size_t xs = xtma_smem<T>(thr * K, D.hx);
+    return D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM;
 }
 
 template <typename T>
@@ -2334,6 +2352,7 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
     template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
+    template int xsolver_staged<T>(const Dev<T> &, int);                                         \
     template cudaError_t launch_extract<T>(const Dev<T> &, cudaStream_t, int, int, T *);         \
     template cudaError_t launch_mass<T>(const Dev<T> &, cudaStream_t, int, double *, int);
 BSQ_INST(float)

@@ -15,6 +15,7 @@ template <typename T> int ysplit_chunks(int ny);
 template <typename T> cudaError_t configure(int nx);
 template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
+template <typename T> int xsolver_staged(const Dev<T> &D, int nx);
 template <typename T> cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, int wc);
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
