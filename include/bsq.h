@@ -85,11 +85,14 @@ typedef struct {
     int kahan;             /* FP32: compensated accumulation of w, P, Q increments */
     int cross_mode;        /* BSQ_CROSS_* */
     int graph_steps;       /* steps per captured CUDA graph in bsq_advance; <= 0: 16 */
-    int tune[4];           /* kernel shape knobs, 0 = default: [0] y-solver rows per thread
-                              (8, 16, 32), [1] y-solver threads per block (32..512),
-                              [2] bit 0: RHS kernel (0 sliding window, 1 shared-memory
-                              tiles); bit 1: x-solver without TMA staging,
-                              [3] rows per warp of the sliding window (16, 32, 64) */
+    int tune[8];           /* kernel shape knobs, 0 = default: [0] block-scan y-solver rows per
+                              thread (8, 16, 32), [1] its threads per block (32..512) -- either
+                              selects the block-scan y-solver over the three-launch one;
+                              [2] bit 0: RHS kernel (0 sliding window, 1 shared-memory tiles),
+                              bit 1: x-solver without shared-memory staging; [3] rows per warp
+                              of the sliding window (16, 32, 64); [4] x-solver elements per
+                              thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
+                              y-solver (8, 16); [6], [7] reserved */
 } bsq_params;
 
 typedef struct {

@@ -30,7 +30,7 @@ class bsq_params(ctypes.Structure):
         ("friction", ctypes.c_double), ("theta", ctypes.c_double), ("eps", ctypes.c_double),
         ("w_s", ctypes.c_double), ("ramp_time", ctypes.c_double), ("timeout_s", ctypes.c_double),
         ("precision", ctypes.c_int), ("kahan", ctypes.c_int), ("cross_mode", ctypes.c_int),
-        ("graph_steps", ctypes.c_int), ("tune", ctypes.c_int * 4),
+        ("graph_steps", ctypes.c_int), ("tune", ctypes.c_int * 8),
     ]
 
 

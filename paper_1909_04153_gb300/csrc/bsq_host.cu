@@ -145,7 +145,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     const bsq_params &p = dm->p;
     const int nx = p.nx, ny = p.ny;
     const int hx = 16 / (int)sizeof(T);
-    const int pitch = row_pitch<T>(nx);  // covers hx + the x-solver's last chunk + 1
+    const int pitch = row_pitch<T>(nx, p.tune[4]);  // covers hx + the x-solver's last chunk + 1
     const int rows = ny + 4;
     const long long fs = (long long)pitch * rows;
     // field stride: padded field rounded up to 256 bytes (the history ring is
@@ -310,7 +310,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     size_t o_ctl = take(sizeof(Ctl)), o_coef = take(sizeof(Coef));
     dm->mass_blocks = 512;
     size_t o_mass = take(dm->mass_blocks * sizeof(double));
-    const size_t nchy = (size_t)ysplit_chunks<T>(ny) * nx;
+    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;  // room for the smallest chunks
     size_t o_ysum = take(7 * nchy * sizeof(T));
     dm->dbytes = off;
     if (cudaMalloc(&dm->dmem, off) != cudaSuccess) { dm->dmem = nullptr; return BSQ_ERR_OOM; }
@@ -331,6 +331,8 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_xtma = (p.tune[2] & 2) ? 1 : 0;
+    D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
+    D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
     {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -372,7 +374,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     dm->coef = D.coef;
     dm->mass_partial = (double *)(base + o_mass);
     // explicit y-solver shapes, or columns of more than 256 chunks, select the block-scan kernel
-    D.ysplit = (p.tune[0] == 0 && p.tune[1] == 0 && ysplit_chunks<T>(ny) <= 256) ? 1 : 0;
+    D.ysplit = (p.tune[0] == 0 && p.tune[1] == 0 && ysplit_chunks<T>(ny, D.tune_yk) <= 256) ? 1 : 0;
     D.ysums = (T *)(base + o_ysum);
     D.yin = D.ysums + 5 * nchy;
     D.yxa = D.ysums + 6 * nchy;

@@ -57,6 +57,7 @@ struct Dev {
     int tune_rhs, tune_rows;       // RHS kernel variant (0 sliding window, 1 tiled), rows per warp
     int tune_xtma;                 // 0: TMA-staged x-solver when it fits, 1: register version
     int nsm;                       // multiprocessors of the device
+    int tune_xk, tune_yk;          // x-solver elements per thread, split y-solver rows per chunk (0: default)
     int ysplit;                    // 1: three-launch y-solver (summaries, scans, apply)
     T *ysums, *yin, *yxa;          // its chunk summaries (5 per chunk) and scanned values
     int bc[4];

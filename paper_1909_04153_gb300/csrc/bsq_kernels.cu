@@ -87,7 +87,17 @@ __device__ void maker_state(const Dev<T> &D, double x, double y, double t, doubl
 {
     double se = 0.0, sp = 0.0, sq = 0.0;
     for (int k = 0; k < D.ncomp; k++) {
-        double ek = D.amp[k] * cos(D.kx[k] * x + D.ky[k] * y - D.om[k] * t + D.ph[k]);
+        const double ph = D.kx[k] * x + D.ky[k] * y - D.om[k] * t + D.ph[k];
+        double c;
+        if (sizeof(T) == 4) {
+            // single-precision path: reduce the phase to [-pi, pi] in FP64,
+            // then a single-precision cosine of the reduced angle
+            const double red = ph - 6.283185307179586 * rint(ph * 0.15915494309189535);
+            c = (double)cosf((float)red);
+        } else {
+            c = cos(ph);
+        }
+        double ek = D.amp[k] * c;
         se += ek;
         sp += D.cx[k] * ek;
         sq += D.cy[k] * ek;
@@ -1083,14 +1093,22 @@ __global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums,
     if (i >= nx) return;
     const long long s = (long long)nx * nch, base = (long long)i * nch;
     constexpr int CPL = 8;  // chunks per lane (nch <= 256)
-    // forward: lane composes its chunks, warp scan, exclusive values per chunk
-    T A = (T)1, B = (T)0;
-    T a_[CPL], b_[CPL];
+    // all five summaries of the lane's chunks are loaded up front
+    T a_[CPL], b_[CPL], s2[CPL], s3[CPL], s4[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; q++) {
         const int k = lane * CPL + q;
-        a_[q] = k < nch ? sums[base + k] : (T)1;
-        b_[q] = k < nch ? sums[s + base + k] : (T)0;
+        const bool v = k < nch;
+        a_[q] = v ? sums[base + k] : (T)1;
+        b_[q] = v ? sums[s + base + k] : (T)0;
+        s2[q] = v ? sums[2 * s + base + k] : (T)0;
+        s3[q] = v ? sums[3 * s + base + k] : (T)0;
+        s4[q] = v ? sums[4 * s + base + k] : (T)1;
+    }
+    // forward: lane composes its chunks, warp scan, exclusive values per chunk
+    T A = (T)1, B = (T)0;
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
         B = a_[q] * B + b_[q];
         A = a_[q] * A;
     }
@@ -1111,9 +1129,8 @@ __global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums,
     T al = (T)0, bb = (T)1;
 #pragma unroll
     for (int q = 0; q < CPL; q++) {
-        const int k = lane * CPL + q;
-        a_[q] = k < nch ? sums[2 * s + base + k] + sums[3 * s + base + k] * yk[q] : (T)0;
-        b_[q] = k < nch ? sums[4 * s + base + k] : (T)1;
+        a_[q] = s2[q] + s3[q] * yk[q];
+        b_[q] = s4[q];
     }
 #pragma unroll
     for (int q = CPL - 1; q >= 0; q--) { al = a_[q] + b_[q] * al; bb = b_[q] * bb; }
@@ -1842,26 +1859,6 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         const long long rowo = fidx(D, 0, j);
         T *sdU = S, *sm = S + span, *se = S + 2 * span, *sc = S + 3 * span, *sP = S + 4 * span;
         T *scP = S + 5 * span, *sw = S + 6 * span, *sH = S + 7 * span;
-        if (seq) {
-            T *qrow[3] = {sH + 1 * hspan + hx, sH + 0 * hspan + hx, sH + 2 * hspan + hx};
-            if (t < 3) {
-                const int rr = j - 1 + t;
-                if (rr >= 0 && rr < ny) {
-                    T *row = qrow[t];
-                    row[-1] = D.bc[SW] == MAKER ? D.mqW[rr] : row[0];
-                    row[nx] = D.bc[SE] == MAKER ? D.mqE[rr] : row[nx - 1];
-                }
-            }
-            __syncthreads();
-            if (j == 0 || j == ny - 1) {
-                const int side = j == 0 ? SS : SN;
-                T *dst = j == 0 ? qrow[0] : qrow[2];
-                const T *src = qrow[1];
-                const T *mq = side == SS ? D.mqS : D.mqN;
-                for (int c = t - 1; c <= nx; c += blockDim.x) dst[c] = D.bc[side] == MAKER ? mq[c + 1] : -src[c];
-            }
-            __syncthreads();
-        }
         T r[K], m[K], e[K];
         vload_k<T, K>(sdU + ib, r);
         vload_k<T, K>(sm + ib, m);
@@ -1877,6 +1874,34 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
             vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
             vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
+            // ghosts of Q^{n+1} at t_{n+1}: columns -1 and nx (W/E rule) in rows
+            // j-1, j, j+1 inside the domain, then the whole ghost row (S/N rule)
+            // when row j-1 or j+1 lies outside; each thread fixes what it reads
+            if (ib == 0) {
+                if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
+                Qc[0] = D.bc[SW] == MAKER ? D.mqW[j] : Qc[1];
+                if (j + 1 < ny) qp[0] = D.bc[SW] == MAKER ? D.mqW[j + 1] : qp[1];
+            }
+            if (nx - 1 >= ib && nx - 1 < ib + K) {
+                const int qe = nx - ib;  // index of column nx in the halo arrays
+#pragma unroll
+                for (int q = 1; q <= K; q++)
+                    if (q == qe) {
+                        if (j - 1 >= 0) qm[q + 1] = D.bc[SE] == MAKER ? D.mqE[j - 1] : qm[q];
+                        Qc[q + 1] = D.bc[SE] == MAKER ? D.mqE[j] : Qc[q];
+                        if (j + 1 < ny) qp[q + 1] = D.bc[SE] == MAKER ? D.mqE[j + 1] : qp[q];
+                    }
+            }
+            if (j == 0 || j == ny - 1) {
+                const int side = j == 0 ? SS : SN;
+                const T *mq = side == SS ? D.mqS : D.mqN;  // maker Q at columns -1..nx
+                T *g = j == 0 ? qm : qp;
+#pragma unroll
+                for (int q = 0; q < K + 2; q++) {
+                    const int c = ib - 1 + q;
+                    g[q] = D.bc[side] == MAKER ? mq[min(max(c, -1), nx) + 1] : -Qc[q];
+                }
+            }
 #pragma unroll
             for (int q = 0; q < K; q++) {
                 T d = tmax(D.w_s - bc_[q + 1], (T)0);
@@ -2141,9 +2166,15 @@ static void ysolve_shape(const Dev<T> &D, int &CW, int &NCH, int &kch)
 }
 
 template <typename T>
-int ysplit_chunks(int ny)
+static int ysplit_rows(int tune)
 {
-    const int KY = sizeof(T) == 4 ? 16 : 8;
+    return tune > 0 ? tune : 8;
+}
+
+template <typename T>
+int ysplit_chunks(int ny, int tune)
+{
+    const int KY = ysplit_rows<T>(tune);
     return (ny + KY - 1) / KY;
 }
 
@@ -2155,20 +2186,21 @@ int step_shape_ok(int nx, int ny)
     return (ny + 31) / 32 <= 512 && nx <= 512 * 32;
 }
 
-// x-solver chunk: elements per thread (a multiple of the vector width)
+// x-solver chunk: elements per thread (a multiple of the vector width), at
+// most 512 threads per row
 template <typename T>
-int x_chunk(int nx)
+int x_chunk(int nx, int tune)
 {
-    // at most 512 threads per row
-    int K = sizeof(T) == 4 ? 8 : 4;
+    int K = tune > 0 ? tune : 4;
+    if (K < VecT<T>::N) K = VecT<T>::N;
     while (K < 32 && (nx + K - 1) / K > 512) K *= 2;
     return K;
 }
 
 template <typename T>
-int row_pitch(int nx)
+int row_pitch(int nx, int tune)
 {
-    int span = 32 * x_chunk<T>(nx);
+    int span = 32 * x_chunk<T>(nx, tune);
     return ((nx + span - 1) / span) * span + span;
 }
 
@@ -2218,7 +2250,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         dim3 g1((nx + TX - 1) / TX, (ny + TY - 1) / TY);
         k_rhs_combine<T, TX, TY><<<g1, dim3(TX, TY), 0, st>>>(D);
     } else {
-        const int rows = D.tune_rows > 0 ? D.tune_rows : 32;
+        const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
         const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
         const int nband = (ny + rows - 1) / rows;
         const long long nwarp = (long long)nstrip * nband;
@@ -2237,12 +2269,14 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (D.ysplit) {
-        constexpr int KY = sizeof(T) == 4 ? 16 : 8;
+        const int KY = ysplit_rows<T>(D.tune_yk);
         const int nch = (ny + KY - 1) / KY;
         dim3 gb2((nx + 31) / 32, (nch + 7) / 8);
-        k_ysum<T, KY><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+        if (KY == 8) k_ysum<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+        else k_ysum<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
         k_yscan<T><<<(int)(((long long)nx * 32 + 255) / 256), 256, 0, st>>>(D, nch, D.ysums, D.yin, D.yxa);
-        k_yapply<T, KY><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
+        if (KY == 8) k_yapply<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
+        else k_yapply<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
     } else {
         int CW, NCH, kch;
         ysolve_shape<T>(D, CW, NCH, kch);
@@ -2253,7 +2287,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         else k_ysolve<T, 16><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
     }
     if (ev) cudaEventRecord(ev[3], st);
-    const int K = x_chunk<T>(nx);
+    const int K = x_chunk<T>(nx, D.tune_xk);
     int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
@@ -2287,7 +2321,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
 template <typename T>
 int xsolver_staged(const Dev<T> &D, int nx)
 {
-    const int K = x_chunk<T>(nx);
+    const int K = x_chunk<T>(nx, D.tune_xk);
     const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const size_t xs = xtma_smem<T>(thr * K, D.hx);
     return D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM;
@@ -2345,8 +2379,8 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
 
 #define BSQ_INST(T)                                                                              \
     template int step_shape_ok<T>(int, int);                                                     \
-    template int row_pitch<T>(int);                                                              \
-    template int ysplit_chunks<T>(int);                                                          \
+    template int row_pitch<T>(int, int);                                                         \
+    template int ysplit_chunks<T>(int, int);                                                     \
     template cudaError_t configure<T>(int);                                                      \
     template cudaError_t launch_step<T>(const Dev<T> &, cudaStream_t, double);                   \
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\

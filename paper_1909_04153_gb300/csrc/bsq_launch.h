@@ -10,8 +10,8 @@
 namespace bsq {
 
 template <typename T> int step_shape_ok(int nx, int ny);
-template <typename T> int row_pitch(int nx);
-template <typename T> int ysplit_chunks(int ny);
+template <typename T> int row_pitch(int nx, int tune);
+template <typename T> int ysplit_chunks(int ny, int tune);
 template <typename T> cudaError_t configure(int nx);
 template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
