@@ -700,7 +700,11 @@ constexpr int SW_COLS = 28;  // interior columns per warp strip (lanes 2..29)
 // x-reconstruction and x-face flux (neighbours by shuffles), bed source,
 // friction, dispersive differences (Eqs. 12-15) and the AB3 combine.  Every
 // reconstruction and every face flux is computed once per strip.
-template <typename T, int ROWS, bool THETA1>
+// FAST: the default configuration fixed at compile time -- sequential cross
+// form, compensated accumulation in single precision, no friction -- with
+// both history levels always read (they hold zeros, weighted by zero, during
+// the Euler start) and 32-bit offsets into the fields.
+template <typename T, int ROWS, bool THETA1, bool FAST>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
 {
     const Coef cf = *D.coef;
@@ -723,7 +727,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
     const T Bg = D.Bd * g, kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
     const T b0c = coefv<T>(cf, 0, 0), b1c = coefv<T>(cf, 0, 1), b2c = coefv<T>(cf, 0, 2);
     const T g0c = coefv<T>(cf, 1, 0), g1c = coefv<T>(cf, 1, 1), g2c = coefv<T>(cf, 1, 2);
-    const bool extrap = D.cross_mode == 0;
+    const bool extrap = FAST ? false : D.cross_mode == 0;
+    const bool kahan = FAST ? (sizeof(T) == 4) : (D.kahan != 0);
+    const int nlev = FAST ? 3 : cf.nlev;
     const long long fs = D.fstride;
     T *H = D.hist;
     const T *corner = D.corner;
@@ -754,16 +760,26 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
         pKR = corner[(long long)(kr + 2) * cp + (kc1 + 2)];
     };
     T hE1 = 0, hF1 = 0, hG1 = 0, hGs1 = 0, hFs1 = 0, hE2 = 0, hF2 = 0, hG2 = 0, hGs2 = 0, hFs2 = 0, hcw = 0;
+    // 32-bit offsets of the history slots (FAST: the fields fit in 2^31 elements)
+    const int ifs = (int)fs, s1o = cf.s1 * (int)fs, s2o = cf.s2 * (int)fs;
     auto load_hist = [&](int o) {
         if (lane_out && o >= j0 && o < ny) {
+            if (FAST) {
+                const int c = (o + 2) * D.pitch + i + D.hx;
+                if (kahan) hcw = D.cw[c];
+                const T *h1 = H + (s1o + c), *h2 = H + (s2o + c);
+                hE1 = h1[0]; hF1 = h1[3 * ifs]; hG1 = h1[6 * ifs]; hGs1 = h1[12 * ifs];
+                hE2 = h2[0]; hF2 = h2[3 * ifs]; hG2 = h2[6 * ifs]; hGs2 = h2[12 * ifs];
+                return;
+            }
             const long long c = fidx(D, i, o);
-            if (D.kahan) hcw = D.cw[c];
-            if (cf.nlev >= 2) {
+            if (kahan) hcw = D.cw[c];
+            if (nlev >= 2) {
                 const long long oo = (long long)cf.s1 * fs + c;
                 hE1 = H[0 * 3 * fs + oo]; hF1 = H[1 * 3 * fs + oo]; hG1 = H[2 * 3 * fs + oo]; hGs1 = H[4 * 3 * fs + oo];
                 if (extrap) hFs1 = H[3 * 3 * fs + oo];
             }
-            if (cf.nlev >= 3) {
+            if (nlev >= 3) {
                 const long long oo = (long long)cf.s2 * fs + c;
                 hE2 = H[0 * 3 * fs + oo]; hF2 = H[1 * 3 * fs + oo]; hG2 = H[2 * 3 * fs + oo]; hGs2 = H[4 * 3 * fs + oo];
                 if (extrap) hFs2 = H[3 * 3 * fs + oo];
@@ -836,7 +852,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
                 T srcx = -g * (bxE - bxW) * rdx * (w0 - (T)0.5 * (bxE + bxW));
                 T srcy = -g * (bN0 - bS0) * rdy * (w0 - (T)0.5 * (bN0 + bS0));
                 T fr1 = (T)0, fr2 = (T)0;
-                if (D.friction != (T)0) {
+                if (!FAST && D.friction != (T)0) {
                     T h = tmax(w0 - bc, (T)0);
                     T iv = (T)BSQ_SQRT2 * h * desing_inv(h, eps);
                     T u = iv * P0, v = iv * Q0;
@@ -875,19 +891,32 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
                 // AB3 / Euler combine (Eqs. 42-43), history prefetched one step ahead
                 T dw = b0c * E, dU = b0c * F, dV = b0c * G + g0c * Gs;
                 if (extrap) dU += g0c * Fs;
-                if (cf.nlev >= 2) {
+                if (nlev >= 2) {
                     dw += b1c * cE1;
                     dU += b1c * cF1;
                     dV += b1c * cG1 + g1c * cGs1;
                     if (extrap) dU += g1c * cFs1;
                 }
-                if (cf.nlev >= 3) {
+                if (nlev >= 3) {
                     dw += b2c * cE2;
                     dU += b2c * cF2;
                     dV += b2c * cG2 + g2c * cGs2;
                     if (extrap) dU += g2c * cFs2;
                 }
                 if (!extrap) dU -= Fs;
+                if (FAST) {
+                    const int ci = (o + 2) * D.pitch + i + D.hx;
+                    T *h0 = H + (cf.s0 * ifs + ci);
+                    h0[0] = E; h0[3 * ifs] = F; h0[6 * ifs] = G; h0[12 * ifs] = Gs;
+                    const T y = kahan ? dw - ccw : dw;
+                    T wnew = w0 + y;
+                    T cwn = kahan ? (wnew - w0) - y : (T)0;
+                    if (wnew < bc) { wnew = bc; cwn = (T)0; nclamp++; }
+                    D.w[cf.wc ^ 1][ci] = wnew;
+                    if (kahan) D.cw[ci] = cwn;
+                    D.dU[ci] = dU;
+                    D.dV[ci] = dV;
+                } else {
                 {
                     const long long oo = (long long)cf.s0 * fs + c;
                     H[0 * 3 * fs + oo] = E;
@@ -897,7 +926,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
                     H[4 * 3 * fs + oo] = Gs;
                 }
                 T wnew, cwn = (T)0;
-                if (D.kahan) {
+                if (kahan) {
                     T y = dw - ccw;
                     wnew = w0 + y;
                     cwn = (wnew - w0) - y;
@@ -906,9 +935,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
                 }
                 if (wnew < bc) { wnew = bc; cwn = (T)0; nclamp++; }
                 D.w[cf.wc ^ 1][c] = wnew;
-                if (D.kahan) D.cw[c] = cwn;
+                if (kahan) D.cw[c] = cwn;
                 D.dU[c] = dU;
                 D.dV[c] = dV;
+                }
             }
             Nprev = Nn;
             Hy0 = h0; Hy1 = h1; Hy2 = h2;
@@ -2255,16 +2285,22 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const int nband = (ny + rows - 1) / rows;
         const long long nwarp = (long long)nstrip * nband;
         const int blocks = (int)((nwarp + 3) / 4);
+        const bool fast = D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 &&
+                          (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
         const bool t1 = D.theta == (T)1;
-        if (rows == 16) {
-            if (t1) k_rhs_sw<T, 16, true><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 16, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        if (fast) {
+            if (rows == 16) k_rhs_sw<T, 16, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+            else if (rows == 32) k_rhs_sw<T, 32, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 64, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+        } else if (rows == 16) {
+            if (t1) k_rhs_sw<T, 16, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 16, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
         } else if (rows == 64) {
-            if (t1) k_rhs_sw<T, 64, true><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 64, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            if (t1) k_rhs_sw<T, 64, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 64, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
         } else {
-            if (t1) k_rhs_sw<T, 32, true><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 32, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            if (t1) k_rhs_sw<T, 32, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 32, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
         }
     }
     if (ev) cudaEventRecord(ev[2], st);
