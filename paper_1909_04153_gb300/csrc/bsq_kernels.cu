@@ -1855,7 +1855,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
     if (!cf.active) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar[2];
-    __shared__ T sA[32], sB[32];
+    __shared__ T sA[32], sB[32], sC[32], sD[32];
     __shared__ double smax[32];
     const int hx = D.hx;
     const int hspan = span + 2 * hx;
@@ -1964,23 +1964,12 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
         if (lane == 0) { Ae = (T)1; Be = (T)0; }
         __syncthreads();
-        if (wid == 0) {
-            T a = lane < nw ? sA[lane] : (T)1, bb = lane < nw ? sB[lane] : (T)0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                T ap = __shfl_up_sync(0xffffffffu, a, o);
-                T bp = __shfl_up_sync(0xffffffffu, bb, o);
-                if (lane >= o) { bb = a * bp + bb; a = a * ap; }
-            }
-            T bx = __shfl_up_sync(0xffffffffu, bb, 1);
-            if (lane == 0) bx = (T)0;
-            if (lane < nw) sB[lane] = bx;
-        }
-        __syncthreads();
-        T y = Ae * sB[wid] + Be;
+        // y entering this warp: the totals of the warps before it, applied in order to y = 0
+        T yw = (T)0;
+        for (int q = 0; q < wid; q++) yw = sA[q] * yw + sB[q];
+        T y = Ae * yw + Be;
 #pragma unroll
         for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
-        __syncthreads();
         T c[K];
         vload_k<T, K>(sc + ib, c);
 #pragma unroll
@@ -1995,24 +1984,14 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             T bp = __shfl_down_sync(0xffffffffu, be, o);
             if (lane + o < 32) { al = al + be * ap; be = be * bp; }
         }
-        if (lane == 0) { sA[wid] = al; sB[wid] = be; }
+        if (lane == 0) { sC[wid] = al; sD[wid] = be; }
         T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
         if (lane == 31) { an = (T)0; bn = (T)1; }
         __syncthreads();
-        if (wid == 0) {
-            T a = lane < nw ? sA[lane] : (T)0, bb = lane < nw ? sB[lane] : (T)1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                T ap = __shfl_down_sync(0xffffffffu, a, o);
-                T bp = __shfl_down_sync(0xffffffffu, bb, o);
-                if (lane + o < 32) { a = a + bb * ap; bb = bb * bp; }
-            }
-            T ax = __shfl_down_sync(0xffffffffu, a, 1);
-            if (lane == 31) ax = (T)0;
-            if (lane < nw) sA[lane] = ax;
-        }
-        __syncthreads();
-        T x = an + bn * sA[wid];
+        // x just after this warp: the totals of the warps after it, from the end
+        T xw = (T)0;
+        for (int q = nw - 1; q > wid; q--) xw = sC[q] + sD[q] * xw;
+        T x = an + bn * xw;
 #pragma unroll
         for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
 
@@ -2059,7 +2038,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             vstore_k<T, K>(Pr + ib, Pv);
             if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
         }
-        __syncthreads();  // this buffer may be refilled from the next iteration on
+        // the wait barrier at the top of the next iteration also releases this buffer
     }
     if (failed) {
         // copies did not complete: flag it, wait (bounded) for what is in
