@@ -89,7 +89,9 @@ typedef struct {
                               thread (8, 16, 32), [1] its threads per block (32..512) -- either
                               selects the block-scan y-solver over the three-launch one;
                               [2] bit 0: RHS kernel (0 sliding window, 1 shared-memory tiles),
-                              bit 1: x-solver without shared-memory staging; [3] rows per warp
+                              bit 1: x-solver without shared-memory staging, bit 2: x-solver
+                              with two rows in flight per block, bit 3: persistent x-solver
+                              with one row in flight; [3] rows per warp
                               of the sliding window (16, 32, 64); [4] x-solver elements per
                               thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
                               y-solver (8, 16); [6], [7] reserved */

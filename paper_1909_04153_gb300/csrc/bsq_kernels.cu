@@ -55,9 +55,10 @@ __device__ __forceinline__ T gslope(T qm, T q0, T qp, T th)
     if (th == (T)1) {
         // theta = 1: the centred difference (a + c)/2 lies between a and c, so
         // the minmod of the three equals the minmod of a and c (bitwise)
-        if (a > (T)0 && c > (T)0) return tmin(a, c);
-        if (a < (T)0 && c < (T)0) return tmax(a, c);
-        return (T)0;
+        // (branch-free: both positive -> the smaller, both negative -> the
+        // larger, otherwise 0)
+        const T mn = tmin(a, c), mx = tmax(a, c);
+        return mn > (T)0 ? mn : (mx < (T)0 ? mx : (T)0);
     }
     return minmod3(th * a, (T)0.5 * (qp - qm), th * c);
 }
@@ -386,9 +387,11 @@ __device__ __forceinline__ void reconstruct(T wm, T w0, T wp, T Pm, T P0, T Pp, 
     T sP = gslope(Pm, P0, Pp, th);
     T sQ = gslope(Qm, Q0, Qp, th);
     T a = w0 + (T)0.5 * sw, b = w0 - (T)0.5 * sw;
-    if (a < bhi) { a = bhi; b = (T)2 * w0 - bhi; }
-    else if (b < blo) { b = blo; a = (T)2 * w0 - blo; }
-    wl = b; wh = a;
+    // positivity: a face value below the face bed is raised to it and the
+    // other face value mirrored about w0 (selects, no branches)
+    const bool hi_low = a < bhi, lo_low = !hi_low && b < blo;
+    wh = hi_low ? bhi : (lo_low ? (T)2 * w0 - blo : a);
+    wl = hi_low ? (T)2 * w0 - bhi : (lo_low ? blo : b);
     Pl = P0 - (T)0.5 * sP; Ph = P0 + (T)0.5 * sP;
     Ql = Q0 - (T)0.5 * sQ; Qh = Q0 + (T)0.5 * sQ;
 }
@@ -668,8 +671,8 @@ __device__ __forceinline__ void cu_flux_st(const FaceSt<T> &L, const FaceSt<T> &
     T ap = tmax(tmax(unL + L.c, unR + R.c), (T)0);
     T am = tmin(tmin(unL - L.c, unR - R.c), (T)0);
     T den = ap - am;
-    if (!(den > (T)0)) { H0 = H1 = H2 = (T)0; return; }
-    T inv = trcp(den);
+    const bool moving = den > (T)0;  // a+ = a- = 0: no flux
+    T inv = trcp(moving ? den : (T)1);
     T pL = L.h * L.u, qL = L.h * L.v, pR = R.h * R.u, qR = R.h * R.v;
     T FL0, FL1, FL2, FR0, FR1, FR2;
     if (DIR == 0) {
@@ -680,9 +683,9 @@ __device__ __forceinline__ void cu_flux_st(const FaceSt<T> &L, const FaceSt<T> &
         FR0 = qR; FR1 = pR * R.v; FR2 = qR * R.v + (T)0.5 * g * R.h * R.h;
     }
     T k = ap * am * inv;
-    H0 = (ap * FL0 - am * FR0) * inv + k * (R.h - L.h);
-    H1 = (ap * FL1 - am * FR1) * inv + k * (pR - pL);
-    H2 = (ap * FL2 - am * FR2) * inv + k * (qR - qL);
+    H0 = moving ? (ap * FL0 - am * FR0) * inv + k * (R.h - L.h) : (T)0;
+    H1 = moving ? (ap * FL1 - am * FR1) * inv + k * (pR - pL) : (T)0;
+    H2 = moving ? (ap * FL2 - am * FR2) * inv + k * (qR - qL) : (T)0;
 }
 
 template <typename T>
@@ -843,7 +846,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
             T dm = shup(dW[1], 1), dp = shdn(dW[1], 1);
             T QSm = shup(QW[0], 1), QSp = shdn(QW[0], 1), QNm = shup(QW[2], 1), QNp = shdn(QW[2], 1);
             T PSm = shup(PW[0], 1), PSp = shdn(PW[0], 1), PNm = shup(PW[2], 1), PNp = shdn(PW[2], 1);
-            if (lane_out && o >= j0 && o < ny) {
+            const bool valid = lane_out && o >= j0 && o < ny;
+            {  // computed on every lane (no divergent region); stores predicated
                 const long long c = fidx(D, i, o);
                 T divx0 = (xe0 - x0) * rdx, divx1 = (xe1 - x1) * rdx, divx2 = (xe2 - x2) * rdx;
                 T divy0 = (h0 - Hy0) * rdy, divy1 = (h1 - Hy1) * rdy, divy2 = (h2 - Hy2) * rdy;
@@ -906,17 +910,22 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
                 if (!extrap) dU -= Fs;
                 if (FAST) {
                     const int ci = (o + 2) * D.pitch + i + D.hx;
-                    T *h0 = H + (cf.s0 * ifs + ci);
-                    h0[0] = E; h0[3 * ifs] = F; h0[6 * ifs] = G; h0[12 * ifs] = Gs;
                     const T y = kahan ? dw - ccw : dw;
                     T wnew = w0 + y;
                     T cwn = kahan ? (wnew - w0) - y : (T)0;
-                    if (wnew < bc) { wnew = bc; cwn = (T)0; nclamp++; }
-                    D.w[cf.wc ^ 1][ci] = wnew;
-                    if (kahan) D.cw[ci] = cwn;
-                    D.dU[ci] = dU;
-                    D.dV[ci] = dV;
-                } else {
+                    const bool cl = wnew < bc;
+                    wnew = cl ? bc : wnew;
+                    cwn = cl ? (T)0 : cwn;
+                    nclamp += (valid && cl) ? 1ull : 0ull;
+                    if (valid) {
+                        T *h0 = H + (cf.s0 * ifs + ci);
+                        h0[0] = E; h0[3 * ifs] = F; h0[6 * ifs] = G; h0[12 * ifs] = Gs;
+                        D.w[cf.wc ^ 1][ci] = wnew;
+                        if (kahan) D.cw[ci] = cwn;
+                        D.dU[ci] = dU;
+                        D.dV[ci] = dV;
+                    }
+                } else if (valid) {
                 {
                     const long long oo = (long long)cf.s0 * fs + c;
                     H[0 * 3 * fs + oo] = E;
@@ -1925,11 +1934,12 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             if (j == 0 || j == ny - 1) {
                 const int side = j == 0 ? SS : SN;
                 const T *mq = side == SS ? D.mqS : D.mqN;  // maker Q at columns -1..nx
-                T *g = j == 0 ? qm : qp;
 #pragma unroll
                 for (int q = 0; q < K + 2; q++) {
                     const int c = ib - 1 + q;
-                    g[q] = D.bc[side] == MAKER ? mq[min(max(c, -1), nx) + 1] : -Qc[q];
+                    const T gv = D.bc[side] == MAKER ? mq[min(max(c, -1), nx) + 1] : -Qc[q];
+                    if (j == 0) qm[q] = gv;  // (no pointer select: keeps both arrays in registers)
+                    else qp[q] = gv;
                 }
             }
 #pragma unroll
@@ -2070,6 +2080,286 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
     }
 }
 
+// ---- two x-lines in flight per block
+//
+// The block's threads form two groups; each group solves its own rows
+// (blockIdx.x * 2 + g, stepping by 2 * gridDim.x) and synchronises on its own
+// named barrier, so one group's scans and epilogue overlap the other's.  The
+// inputs of the forward sweep (dU, m, e and the Q, bC rows j-1..j+1) are
+// staged per group by bulk copies into one buffer, refilled with the next row
+// as soon as the group has read it (at the first scan barrier); c', P, cP and
+// w go straight to registers.  Warp totals are composed by a shuffle scan
+// over the group's warps.  Same arithmetic as k_xsolve.
+constexpr int XG_ARR_PLAIN = 3, XG_ARR_HALO = 6;
+
+template <typename T>
+static size_t xgrp_smem(int span, int hx)
+{
+    return ((size_t)XG_ARR_PLAIN * span + (size_t)XG_ARR_HALO * (span + 2 * hx)) * sizeof(T);
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// barrier over `nthreads` threads that also ORs a predicate across them
+__device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
+{
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void xgrp_issue(const Dev<T> &D, int j, T *S, int span, unsigned long long *bar)
+{
+    const int hx = D.hx, hspan = span + 2 * hx;
+    const long long rowo = fidx(D, 0, j);
+    const bool seq = D.cross_mode != 0;
+    const unsigned pb = (unsigned)(span * sizeof(T)), hb = (unsigned)(hspan * sizeof(T));
+    mbar_expect_tx(bar, 3u * pb + 2u * hb + (seq ? 4u * hb : 0u));
+    tma_load_1d(S + 0 * span, D.dU + rowo, pb, bar);
+    tma_load_1d(S + 1 * span, D.fxm + rowo, pb, bar);
+    tma_load_1d(S + 2 * span, D.fxe + rowo, pb, bar);
+    T *sH = S + 3 * span;
+    const T *Qr = D.Q + rowo - hx, *br = D.bC + rowo - hx;
+    tma_load_1d(sH + 0 * hspan, Qr, hb, bar);
+    tma_load_1d(sH + 3 * hspan, br, hb, bar);
+    if (seq) {
+        tma_load_1d(sH + 1 * hspan, Qr - D.pitch, hb, bar);
+        tma_load_1d(sH + 2 * hspan, Qr + D.pitch, hb, bar);
+        tma_load_1d(sH + 4 * hspan, br - D.pitch, hb, bar);
+        tma_load_1d(sH + 5 * hspan, br + D.pitch, hb, bar);
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(512, 1) k_xsolve_grp(Dev<T> D, int span, double forced_dt_next)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ T sA[2][32], sB[2][32], sC[2][32], sD[2][32];
+    __shared__ double smax[32];
+    const int hx = D.hx, hspan = span + 2 * hx;
+    const int gthr = (int)blockDim.x >> 1;
+    const int t = threadIdx.x, g = t >= gthr ? 1 : 0, tg = t - g * gthr;
+    const int lane = t & 31, wid = tg >> 5, nwg = gthr >> 5, nw = (int)blockDim.x >> 5;
+    T *S = reinterpret_cast<T *>(smem_raw) + (size_t)g * ((size_t)XG_ARR_PLAIN * span + (size_t)XG_ARR_HALO * hspan);
+    const int nx = D.nx, ny = D.ny;
+    const bool seq = D.cross_mode != 0;
+    const int ib = tg * K;
+    const int j0 = (int)blockIdx.x * 2 + g, jstep = (int)gridDim.x * 2;
+    unsigned long long *bg = &bar[g];
+    if (tg == 0) {
+        mbar_init(bg, 1);
+        fence_barrier_init();
+        if (j0 < ny) xgrp_issue(D, j0, S, span, bg);
+    }
+    named_sync(1 + g, gthr);
+    T rate = (T)0;
+    bool bad = false, failed = false;
+    int it = 0;
+    T *wnew = D.w[cf.wc ^ 1];
+    for (int j = j0; j < ny; j += jstep, it++) {
+        const bool ok = mbar_wait_bounded(bg, (unsigned)(it & 1), 1LL << 24);
+        const long long rowo = fidx(D, 0, j);
+        T *sH = S + 3 * span;
+        T r[K], m[K], e[K];
+        vload_k<T, K>(S + ib, r);
+        vload_k<T, K>(S + span + ib, m);
+        vload_k<T, K>(S + 2 * span + ib, e);
+        T Qc[K + 2], bc_[K + 2];
+        load_halo_chunk<T, K>(sH + 0 * hspan + hx, ib, lane, Qc);
+        load_halo_chunk<T, K>(sH + 3 * hspan + hx, ib, lane, bc_);
+        if (seq) {
+            const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+            const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+            T qm[K + 2], qp[K + 2], bm[K], bp[K];
+            load_halo_chunk<T, K>(sH + 1 * hspan + hx, ib, lane, qm);
+            load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
+            vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
+            vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
+            // ghosts of Q^{n+1} at t_{n+1}, as in k_xsolve_pipe
+            if (ib == 0) {
+                if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
+                Qc[0] = D.bc[SW] == MAKER ? D.mqW[j] : Qc[1];
+                if (j + 1 < ny) qp[0] = D.bc[SW] == MAKER ? D.mqW[j + 1] : qp[1];
+            }
+            if (nx - 1 >= ib && nx - 1 < ib + K) {
+                const int qe = nx - ib;
+#pragma unroll
+                for (int q = 1; q <= K; q++)
+                    if (q == qe) {
+                        if (j - 1 >= 0) qm[q + 1] = D.bc[SE] == MAKER ? D.mqE[j - 1] : qm[q];
+                        Qc[q + 1] = D.bc[SE] == MAKER ? D.mqE[j] : Qc[q];
+                        if (j + 1 < ny) qp[q + 1] = D.bc[SE] == MAKER ? D.mqE[j + 1] : qp[q];
+                    }
+            }
+            if (j == 0 || j == ny - 1) {
+                const int side = j == 0 ? SS : SN;
+                const T *mq = side == SS ? D.mqS : D.mqN;
+#pragma unroll
+                for (int q = 0; q < K + 2; q++) {
+                    const int cc = ib - 1 + q;
+                    const T gv = D.bc[side] == MAKER ? mq[min(max(cc, -1), nx) + 1] : -Qc[q];
+                    if (j == 0) qm[q] = gv;  // (no pointer select: keeps both arrays in registers)
+                    else qp[q] = gv;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                T d = tmax(D.w_s - bc_[q + 1], (T)0);
+                T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
+                T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
+                T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
+                T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+                T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+            }
+        }
+        // operands of the back substitution and the epilogue, from memory
+        T c[K], Pv[K], cPv[K], wv[K];
+        vload_k<T, K>(D.fxc + rowo + ib, c);
+        vload_k<T, K>(D.P + rowo + ib, Pv);
+        if (D.kahan) vload_k<T, K>(D.cP + rowo + ib, cPv);
+        vload_k<T, K>(wnew + rowo + ib, wv);
+        const T corrW = D.corrW[j], corrE = D.corrE[j];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            int i = ib + q;
+            if (i == 0) r[q] += corrW;
+            if (i == nx - 1) r[q] += corrE;
+            if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; c[q] = (T)0; }
+        }
+        T A = (T)1, B = (T)0;
+#pragma unroll
+        for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T Ap = __shfl_up_sync(0xffffffffu, A, o);
+            T Bp = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+        }
+        if (lane == 31) { sA[g][wid] = A; sB[g][wid] = B; }
+        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) { Ae = (T)1; Be = (T)0; }
+        if (named_sync_or(1 + g, gthr, !ok)) { failed = true; break; }
+        // every thread of the group has read the staged row: refill it
+        if (tg == 0 && j + jstep < ny) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            xgrp_issue(D, j + jstep, S, span, bg);
+        }
+        // y entering this warp: inclusive scan of the group's warp totals
+        T qa = (T)1, qb = (T)0;
+        if (lane < nwg) { qa = sA[g][lane]; qb = sB[g][lane]; }
+        for (int o = 1; o < nwg; o <<= 1) {
+            T pa = __shfl_up_sync(0xffffffffu, qa, o);
+            T pb = __shfl_up_sync(0xffffffffu, qb, o);
+            if (lane >= o) { qb = qa * pb + qb; qa = qa * pa; }
+        }
+        T yw = __shfl_sync(0xffffffffu, qb, (wid + 31) & 31);
+        if (wid == 0) yw = (T)0;
+        T y = Ae * yw + Be;
+#pragma unroll
+        for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
+        T al = (T)0, be = (T)1;
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, al, o);
+            T bp = __shfl_down_sync(0xffffffffu, be, o);
+            if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+        }
+        if (lane == 0) { sC[g][wid] = al; sD[g][wid] = be; }
+        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
+        if (lane == 31) { an = (T)0; bn = (T)1; }
+        named_sync(1 + g, gthr);
+        // x just after this warp: suffix scan of the group's warp totals
+        T qc = (T)0, qd = (T)1;
+        if (lane < nwg) { qc = sC[g][lane]; qd = sD[g][lane]; }
+        for (int o = 1; o < nwg; o <<= 1) {
+            T pc = __shfl_down_sync(0xffffffffu, qc, o);
+            T pd = __shfl_down_sync(0xffffffffu, qd, o);
+            if (lane + o < 32) { qc = qc + qd * pc; qd = qd * pd; }
+        }
+        T xw = __shfl_sync(0xffffffffu, qc, (wid + 1) & 31);
+        if (wid == nwg - 1) xw = (T)0;
+        T x = an + bn * xw;
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
+
+        T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo, *wrow = wnew + rowo;
+        const T *Qv = Qc + 1, *bv = bc_ + 1;
+        const T gyj = D.gy[j];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const int i = ib + q;
+            if (i >= nx) continue;
+            T Pn, cn = (T)0;
+            if (D.kahan) {
+                T yy = r[q] - cPv[q];
+                Pn = Pv[q] + yy;
+                cn = (Pn - Pv[q]) - yy;
+            } else {
+                Pn = Pv[q] + r[q];
+            }
+            T wq = wv[q];
+            T gm = D.gx[i] * gyj;
+            if (gm < (T)1) {
+                T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
+                wq = bv[q] + (d + gm * (h - d));
+                wrow[i] = wq;
+                if (D.kahan) cwr[i] = (T)0;
+                Pn *= gm;
+                cn *= gm;
+            }
+            Pv[q] = Pn;
+            cPv[q] = cn;
+            T h = tmax(wq - bv[q], (T)0);
+            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
+            T u = iv * Pn, v = iv * Qv[q];
+            T cc = tsqrt(D.g * h);
+            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+        }
+        if (ib < nx) {
+            vstore_k<T, K>(Pr + ib, Pv);
+            if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+        }
+    }
+    if (failed) {
+        // copies did not complete: wait (bounded) for what is in flight and
+        // let the controller of the next step stop the run
+        mbar_wait_bounded(bg, (unsigned)(it & 1), 1LL << 22);
+    }
+    __syncthreads();
+    double rr = (double)rate;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    bool anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) smax[t >> 5] = anybad ? -1.0 : rr;
+    const bool anyfailed = __syncthreads_or(failed);
+    if (t == 0) {
+        double mx = 0.0;
+        bool fl = false;
+        for (int q = 0; q < nw; q++) {
+            if (smax[q] < 0.0) fl = true;
+            else mx = fmax(mx, smax[q]);
+        }
+        if (anyfailed) atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
+        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
+        atomicMax(&D.ctl->rate_bits, dbits(mx));
+        next_step_controller(D, anyfailed ? 0.0 : forced_dt_next);
+    }
+}
+
 // shared memory bytes of the TMA x-solver for a row span
 template <typename T>
 static size_t xtma_smem(int span, int hx)
@@ -2196,11 +2486,12 @@ int step_shape_ok(int nx, int ny)
 }
 
 // x-solver chunk: elements per thread (a multiple of the vector width), at
-// most 512 threads per row
+// most 512 threads per row; by default 8 in single precision (two rows of
+// up to 2048 cells in flight per block), 4 in double precision
 template <typename T>
 int x_chunk(int nx, int tune)
 {
-    int K = tune > 0 ? tune : 4;
+    int K = tune > 0 ? tune : (sizeof(T) == 4 ? 8 : 4);
     if (K < VecT<T>::N) K = VecT<T>::N;
     while (K < 32 && (nx + K - 1) / K > 512) K *= 2;
     return K;
@@ -2237,7 +2528,30 @@ cudaError_t configure(int nx)
         e = cudaFuncSetAttribute(k_xsolve_pipe<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_pipe<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_grp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_grp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     return e;
+}
+
+// x-solver variants (tune_xtma): 0 automatic -- the two-group kernel in
+// single precision where a row takes at most 256 threads of K = 4 or 8
+// elements and both staging buffers fit, else the one-row persistent kernel,
+// else the per-row staged kernel, else registers only; 1 registers only;
+// 2 the two-group kernel where it fits; 3 the one-row persistent kernel.
+template <typename T>
+static bool xsolver_grouped(const Dev<T> &D, int nx)
+{
+    const int K = x_chunk<T>(nx, D.tune_xk);
+    const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
+    const bool want = D.tune_xtma == 2 || (D.tune_xtma == 0 && sizeof(T) == 4);
+    return want && (K == 4 || K == 8) && thr <= 256 && 2 * xgrp_smem<T>(thr * K, D.hx) <= XPIPE_MAX_SMEM;
+}
+template <typename T>
+static bool xsolver_staging_allowed(const Dev<T> &D)
+{
+    return D.tune_xtma == 0 || D.tune_xtma == 3;
 }
 
 // One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
@@ -2306,14 +2620,20 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
-    const bool pipe = D.tune_xtma == 0 && 2 * xs <= XPIPE_MAX_SMEM;
-    const bool tma = pipe || (D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM);
+    const bool grp = xsolver_grouped(D, nx);
+    const bool pipe = !grp && xsolver_staging_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM;
+    const bool tma = grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
     if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (pipe) {
+    if (grp) {
+        const int grid = min((ny + 1) / 2, D.nsm);
+        const size_t gs = 2 * xgrp_smem<T>(span, D.hx);
+        if (K == 4) k_xsolve_grp<T, 4><<<grid, 2 * thr, gs, st>>>(D, span, forced_dt_next);
+        else k_xsolve_grp<T, 8><<<grid, 2 * thr, gs, st>>>(D, span, forced_dt_next);
+    } else if (pipe) {
         const int grid = min(ny, D.nsm);
         if (K == 4) k_xsolve_pipe<T, 4><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
         else if (K == 8) k_xsolve_pipe<T, 8><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
@@ -2339,7 +2659,7 @@ int xsolver_staged(const Dev<T> &D, int nx)
     const int K = x_chunk<T>(nx, D.tune_xk);
     const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const size_t xs = xtma_smem<T>(thr * K, D.hx);
-    return D.tune_xtma == 0 && xs <= XTMA_MAX_SMEM;
+    return xsolver_grouped(D, nx) || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
 }
 
 template <typename T>
