@@ -228,7 +228,7 @@ def run_ours(args):
     prec = args.precision
     fp = "fp32" if prec == "fp32" else "fp64"
     dom = bsq.Domain(case, precision=prec, kahan=(prec == "fp32"), stream=stream.cuda_stream,
-                     graph_steps=args.graph_steps)
+                     graph_steps=args.graph_steps, tune=args.tune)
     # warm-up (also builds the CUDA graph)
     dom.advance(max_steps=args.warmup)
     torch.cuda.synchronize(dev)
@@ -292,7 +292,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     d2 = bsq.Domain(case, precision=prec, kahan=(prec == "fp32"), stream=stream.cuda_stream,
-                    graph_steps=args.graph_steps)
+                    graph_steps=args.graph_steps, tune=args.tune)
     d2.advance(max_steps=args.steps)
     eta = d2.read("eta")
     t_e2e = time.perf_counter() - t0
@@ -361,6 +361,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=40)
+    ap.add_argument("--tune", type=lambda s: tuple(int(v) for v in s.split(",")), default=None,
+                    help="kernel shape knobs (bsq_params.tune), comma separated")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -182,6 +182,48 @@ const char *bsq_kernel_name(int k);
  * 0 for a NULL handle. */
 int bsq_launches_per_step(const bsq_domain *d);
 
+/* ---- Batches: many domains advanced together (one launch per stage).
+ *
+ * The per-step update of every member is the single-domain one (Sec. 3, Eqs.
+ * 5-22, 42-47), each member with its own adaptive dt, AB3 history, time and
+ * limits: the batch only changes how the work is launched.  Every stage of a
+ * step (ghost cells, RHS + combine, the three y-line launches, the x-line
+ * solves) is one kernel launch over the blocks of all members, captured in
+ * CUDA graphs of graph_steps steps; a member that has reached its t_end or
+ * step limit (or failed) does no work in later steps while the others go on.
+ * The batch does not own the domains: they stay valid handles (bsq_read,
+ * bsq_info, bsq_checkpoint, bsq_advance on their own), must outlive the batch,
+ * and must not be used on their own while a batch call runs.  x-lines use the
+ * warp-per-row solver, so a member advanced alone gives the same result
+ * bitwise when created with tune[2] = 16 (and otherwise the same result up to
+ * rounding order). */
+typedef struct bsq_batch bsq_batch;
+
+/* Group n distinct domains of the same precision, Kahan setting and cross
+ * mode, created with default tune[0], [1], [4], [5], rows of at most 6144
+ * (FP32) / 3072 (FP64) cells and ny <= 2048.  cuda_stream: the stream batch
+ * calls run on; NULL = a stream the library creates.  Builds the per-stage
+ * block tables on the device.  Errors: BSQ_ERR_ARG (mixed or unsupported
+ * members, a member in an error state, repeated handles), BSQ_ERR_OOM,
+ * BSQ_ERR_CUDA.  On error *out is NULL. */
+bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *cuda_stream, bsq_batch **out);
+
+/* Advance every member d until its own t_end[d] (NULL: no time limit for all)
+ * or max_steps more steps (<= 0: no step limit; then every t_end must be
+ * finite).  steps_done (NULL or n entries) receives the steps each member took.
+ * Waits (bounded) for each member's own stream first.  A member that fails
+ * (BSQ_ERR_NONFINITE, BSQ_ERR_UNSTABLE) stops, keeps that status as its sticky
+ * error, and the others finish; the first such status is returned.  Other
+ * errors: BSQ_ERR_ARG, BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
+bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long long max_steps, long long *steps_done);
+
+/* Members of the batch; kernel launches per batched step. */
+int bsq_batch_size(const bsq_batch *b);
+int bsq_batch_launches_per_step(const bsq_batch *b);
+
+/* Release the batch (not its domains); NULL-safe. */
+void bsq_batch_destroy(bsq_batch *b);
+
 /* Allocation-free variant of the volume reduction that bsq_info's mass uses.
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc, such as an application that owns every byte of device memory

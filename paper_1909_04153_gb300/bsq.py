@@ -93,6 +93,15 @@ def lib():
         L.bsq_kernel_name.argtypes = [ctypes.c_int]
         L.bsq_launches_per_step.restype = ctypes.c_int
         L.bsq_launches_per_step.argtypes = [vp]
+        L.bsq_batch_create.restype = ctypes.c_int
+        L.bsq_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.bsq_batch_advance.restype = ctypes.c_int
+        L.bsq_batch_advance.argtypes = [vp, _DP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.bsq_batch_size.restype = ctypes.c_int
+        L.bsq_batch_size.argtypes = [vp]
+        L.bsq_batch_launches_per_step.restype = ctypes.c_int
+        L.bsq_batch_launches_per_step.argtypes = [vp]
+        L.bsq_batch_destroy.argtypes = [vp]
         L.bsq_mass_noalloc.restype = ctypes.c_int
         L.bsq_mass_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                        ctypes.c_double, ctypes.c_double, vp, vp]
@@ -211,6 +220,29 @@ def bsq_kernel_name(k: int) -> str:
     return lib().bsq_kernel_name(int(k)).decode()
 
 
+def bsq_batch_create(handles, stream: int | None = None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    h = ctypes.c_void_p()
+    st = lib().bsq_batch_create(arr, len(handles), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    if st != OK:
+        raise BsqError(st, "bsq_batch_create")
+    return h
+
+
+def bsq_batch_advance(h, n: int, t_end=None, max_steps: int = 0) -> np.ndarray:
+    te = None if t_end is None else _f64(np.broadcast_to(np.asarray(t_end, dtype=np.float64), (n,)))
+    steps = (ctypes.c_longlong * n)()
+    st = lib().bsq_batch_advance(h, _ptr(te), int(max_steps), steps)
+    if st != OK:
+        raise BsqError(st, "bsq_batch_advance")
+    return np.array(steps[:], dtype=np.int64)
+
+
+def bsq_batch_destroy(h) -> None:
+    if h:
+        lib().bsq_batch_destroy(h)
+
+
 NOALLOC_MAX_ROWS = 16384
 
 
@@ -318,3 +350,38 @@ class Domain:
 
     def launches_per_step(self) -> int:
         return lib().bsq_launches_per_step(self.h)
+
+
+class Batch:
+    """Several :class:`Domain` objects advanced together, one launch per stage
+    (``bsq_batch_*``).  The domains stay usable on their own between calls and
+    must outlive the batch."""
+
+    def __init__(self, domains, stream: int | None = None):
+        self.domains = list(domains)
+        self.h = bsq_batch_create([d.h for d in self.domains], stream)
+
+    def advance(self, t_end=None, max_steps: int = 0) -> np.ndarray:
+        """Per-domain steps taken; t_end is one time for all, a sequence of
+        per-domain times, or None (then max_steps > 0)."""
+        return bsq_batch_advance(self.h, len(self.domains), t_end, max_steps)
+
+    def launches_per_step(self) -> int:
+        return lib().bsq_batch_launches_per_step(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            bsq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

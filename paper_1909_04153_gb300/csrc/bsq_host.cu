@@ -303,7 +303,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     size_t o_fields = take(fb * nfields);
     size_t o_corner = take(cornerT.size() * sizeof(T));
-    size_t o_gx = take(nx * sizeof(T)), o_gy = take(ny * sizeof(T));
+    size_t o_gx = take((size_t)pitch * sizeof(T)), o_gy = take(ny * sizeof(T));  // gx: row-length vector loads
     size_t o_corr = take((size_t)(4 * nx + 4 * ny + 4) * sizeof(T));
     size_t o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
     size_t o_comp = take(comp.size() * sizeof(double));
@@ -330,7 +330,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_ythreads = p.tune[1] >= 32 && p.tune[1] <= 512 ? p.tune[1] : 0;
     D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
-    D.tune_xtma = (p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0));
+    D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
     {
@@ -615,6 +615,263 @@ extern "C" bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n)
     if (st != BSQ_OK) return set_sticky(d, st);
     return set_sticky(d, ctl_status(*d->h_ctl));
 }
+
+// ------------------------------------------------------------------ batches
+
+struct bsq_batch {
+    std::vector<bsq_domain *> doms;
+    int fp64;
+    cudaStream_t stream;
+    int own_stream;
+    void *dmem;          // descriptors, block tables, t_end, gathered Ctl
+    void *Ds;            // Dev<T>[n]
+    double *d_tend, *h_tend;
+    Ctl *d_ctl, *h_ctl;  // gathered controller states (h_ctl pinned)
+    BatchPlan plan;
+    cudaGraphExec_t graph;
+    int graph_steps;
+    double timeout_s;
+};
+
+static bsq_status wait_batch(const bsq_batch *b)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    int us = 20;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(b->stream);
+        if (e == cudaSuccess) return BSQ_OK;
+        if (e != cudaErrorNotReady) return BSQ_ERR_CUDA;
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > b->timeout_s) return BSQ_ERR_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(us));
+        if (us < 1000) us *= 2;
+    }
+}
+
+static void batch_free(bsq_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->h_tend) cudaFreeHost(b->h_tend);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// The block tables of every stage for the member domains; each domain's
+// blocks are laid out exactly as its own single-domain launches lay them out.
+template <typename T>
+static bsq_status batch_build(bsq_batch *b)
+{
+    const int n = (int)b->doms.size();
+    std::vector<int4> tg, tr, ts, tc, tx;
+    bool fast = true, theta1 = true;
+    const int K = batch_xchunk<T>();
+    int yrow_max = 32 * K;
+    std::vector<Dev<T>> hD(n);
+    for (int d = 0; d < n; d++) {
+        const Dev<T> &D = dev_of<T>(b->doms[d]);
+        hD[d] = D;
+        const int nx = D.nx, ny = D.ny;
+        if (!D.ysplit || D.tune_yk != 0 || D.tune_xk != 0) return BSQ_ERR_ARG;
+        fast = fast && D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 &&
+               (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
+        theta1 = theta1 && D.theta == (T)1;
+        const long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
+        const int gb = (int)((nwork + 255) / 256);
+        for (int q = 0; q < gb; q++) tg.push_back(make_int4(d, q, gb, 0));
+        const int nstrip = (nx + 27) / 28, nband = (ny + 63) / 64;
+        const int rb = (int)(((long long)nstrip * nband + 3) / 4);
+        for (int q = 0; q < rb; q++) tr.push_back(make_int4(d, q, nstrip, 0));
+        const int nch = (ny + 7) / 8;
+        const int gx = (nx + 31) / 32, gy = (nch + 7) / 8;
+        for (int by = 0; by < gy; by++)
+            for (int bx = 0; bx < gx; bx++) ts.push_back(make_int4(d, bx, by, nch));
+        const int cb = (int)(((long long)nx * 32 + 255) / 256);
+        for (int q = 0; q < cb; q++) tc.push_back(make_int4(d, q, nch, 0));
+        const int yrow = (nx + 32 * K - 1) / (32 * K) * (32 * K);
+        if (yrow > yrow_max) yrow_max = yrow;
+        const int xb = (ny + 3) / 4;
+        for (int q = 0; q < xb; q++) tx.push_back(make_int4(d, q, xb, yrow));
+    }
+    if ((size_t)4 * yrow_max * sizeof(T) > 96 * 1024) return BSQ_ERR_ARG;  // rows longer than the x-solver holds
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    const size_t o_D = take(n * sizeof(Dev<T>));
+    const size_t o_g = take(tg.size() * sizeof(int4)), o_r = take(tr.size() * sizeof(int4));
+    const size_t o_s = take(ts.size() * sizeof(int4)), o_c = take(tc.size() * sizeof(int4));
+    const size_t o_x = take(tx.size() * sizeof(int4));
+    const size_t o_t = take(n * sizeof(double)), o_ctl = take(n * sizeof(Ctl));
+    if (cudaMalloc(&b->dmem, off) != cudaSuccess) { b->dmem = nullptr; return BSQ_ERR_OOM; }
+    char *base = (char *)b->dmem;
+    CK(cudaMemcpy(base + o_D, hD.data(), n * sizeof(Dev<T>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(base + o_g, tg.data(), tg.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(base + o_r, tr.data(), tr.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(base + o_s, ts.data(), ts.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(base + o_c, tc.data(), tc.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(base + o_x, tx.data(), tx.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->Ds = base + o_D;
+    b->d_tend = (double *)(base + o_t);
+    b->d_ctl = (Ctl *)(base + o_ctl);
+    BatchPlan &P = b->plan;
+    P.n = n;
+    P.nb_ghost = (int)tg.size(); P.nb_rhs = (int)tr.size(); P.nb_ysum = (int)ts.size();
+    P.nb_yscan = (int)tc.size(); P.nb_x = (int)tx.size();
+    P.t_ghost = (const int4 *)(base + o_g); P.t_rhs = (const int4 *)(base + o_r);
+    P.t_ysum = (const int4 *)(base + o_s); P.t_yscan = (const int4 *)(base + o_c);
+    P.t_x = (const int4 *)(base + o_x);
+    P.rhs_fast = fast ? 1 : 0;
+    P.rhs_theta1 = theta1 ? 1 : 0;
+    P.yrow_max = yrow_max;
+    CK(configure_batch<T>(yrow_max));
+    return BSQ_OK;
+}
+
+extern "C" bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *cuda_stream, bsq_batch **out)
+{
+    cudaGetLastError();
+    if (!out) return BSQ_ERR_ARG;
+    *out = nullptr;
+    if (!domains || n < 1) return BSQ_ERR_ARG;
+    for (int d = 0; d < n; d++) {
+        bsq_domain *x = domains[d];
+        if (!x || x->sticky != BSQ_OK) return BSQ_ERR_ARG;
+        if (x->fp64 != domains[0]->fp64 || x->p.kahan != domains[0]->p.kahan ||
+            x->p.cross_mode != domains[0]->p.cross_mode)
+            return BSQ_ERR_ARG;
+        for (int e = 0; e < d; e++)
+            if (domains[e] == x) return BSQ_ERR_ARG;
+    }
+    bsq_batch *b = new (std::nothrow) bsq_batch();
+    if (!b) return BSQ_ERR_OOM;
+    b->doms.assign(domains, domains + n);
+    b->fp64 = domains[0]->fp64;
+    b->graph_steps = domains[0]->graph_steps;
+    b->timeout_s = 0.0;
+    for (int d = 0; d < n; d++) {
+        const double ts = domains[d]->p.timeout_s > 0 ? domains[d]->p.timeout_s : 600.0;
+        if (ts > b->timeout_s) b->timeout_s = ts;
+    }
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            b->stream = nullptr;
+            batch_free(b);
+            return BSQ_ERR_CUDA;
+        }
+        b->own_stream = 1;
+    }
+    if (cudaMallocHost((void **)&b->h_tend, n * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_ctl, n * sizeof(Ctl)) != cudaSuccess) {
+        batch_free(b);
+        return BSQ_ERR_OOM;
+    }
+    bsq_status st = b->fp64 ? batch_build<double>(b) : batch_build<float>(b);
+    if (st != BSQ_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return BSQ_OK;
+}
+
+extern "C" void bsq_batch_destroy(bsq_batch *b) { batch_free(b); }
+
+static bsq_status batch_read_ctl(bsq_batch *b)
+{
+    const int n = (int)b->doms.size();
+    cudaError_t e = b->fp64 ? launch_batch_gather<double>((const Dev<double> *)b->Ds, n, b->d_ctl, b->stream)
+                            : launch_batch_gather<float>((const Dev<float> *)b->Ds, n, b->d_ctl, b->stream);
+    if (e != cudaSuccess) return BSQ_ERR_CUDA;
+    CK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    return wait_batch(b);
+}
+
+extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long long max_steps,
+                                        long long *steps_done)
+{
+    cudaGetLastError();
+    if (!b) return BSQ_ERR_ARG;
+    const int n = (int)b->doms.size();
+    if (steps_done)
+        for (int d = 0; d < n; d++) steps_done[d] = 0;
+    for (int d = 0; d < n; d++) {
+        const double te = t_end ? t_end[d] : INFINITY;
+        if (isnan(te) || (max_steps <= 0 && !isfinite(te))) return BSQ_ERR_ARG;
+        b->h_tend[d] = te;
+    }
+    for (int d = 0; d < n; d++) {
+        if (b->doms[d]->sticky != BSQ_OK) return b->doms[d]->sticky;
+        bsq_status s = wait_stream(b->doms[d]);  // the domain's own work comes first
+        if (s != BSQ_OK) return set_sticky(b->doms[d], s);
+    }
+    bsq_status st = batch_read_ctl(b);
+    if (st != BSQ_OK) return st;
+    std::vector<long long> n0(n);
+    for (int d = 0; d < n; d++) n0[d] = b->h_ctl[d].n;
+    if (!b->graph) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < b->graph_steps && e == cudaSuccess; s++)
+            e = b->fp64 ? launch_batch_step<double>((const Dev<double> *)b->Ds, b->plan, b->stream)
+                        : launch_batch_step<float>((const Dev<float> *)b->Ds, b->plan, b->stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) return BSQ_ERR_CUDA;
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->graph = nullptr; return BSQ_ERR_CUDA; }
+    }
+    CK(cudaMemcpyAsync(b->d_tend, b->h_tend, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    cudaError_t e = b->fp64
+                        ? launch_batch_start<double>((const Dev<double> *)b->Ds, n, b->d_tend, max_steps, b->stream)
+                        : launch_batch_start<float>((const Dev<float> *)b->Ds, n, b->d_tend, max_steps, b->stream);
+    if (e != cudaSuccess) return BSQ_ERR_CUDA;
+    // a domain is finished when it reached its t_end or its step limit, or failed
+    auto all_done = [&]() {
+        for (int d = 0; d < n; d++) {
+            const Ctl &c = b->h_ctl[d];
+            if (ctl_status(c) != BSQ_OK) continue;
+            if (max_steps > 0 && c.n - n0[d] >= max_steps) continue;
+            const double te = b->h_tend[d];
+            const double tol = isfinite(te) ? 1e-12 * fmax(1.0, fabs(te)) : 0.0;
+            if (c.t < te - tol) return false;
+        }
+        return true;
+    };
+    long long launched = 0;
+    const long long cap = max_steps > 0 ? (max_steps + b->graph_steps - 1) / b->graph_steps : -1;
+    int chunk = 1;
+    for (;;) {
+        long long m = chunk;
+        if (cap >= 0 && launched + m > cap) m = cap - launched;
+        for (long long r = 0; r < m; r++)
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return BSQ_ERR_CUDA;
+        launched += m;
+        st = batch_read_ctl(b);
+        if (st != BSQ_OK) return st;
+        if (all_done() || (cap >= 0 && launched >= cap)) break;
+        if (chunk < 64) chunk *= 2;
+    }
+    bsq_status first = BSQ_OK;
+    for (int d = 0; d < n; d++) {
+        if (steps_done) steps_done[d] = b->h_ctl[d].n - n0[d];
+        *b->doms[d]->h_ctl = b->h_ctl[d];
+        bsq_status s = ctl_status(b->h_ctl[d]);
+        if (s != BSQ_OK) {
+            set_sticky(b->doms[d], s);
+            if (first == BSQ_OK) first = s;
+        }
+    }
+    return first;
+}
+
+extern "C" int bsq_batch_size(const bsq_batch *b) { return b ? (int)b->doms.size() : 0; }
+
+extern "C" int bsq_batch_launches_per_step(const bsq_batch *b) { return b ? 6 : 0; }
 
 // ------------------------------------------------------------------ outputs
 

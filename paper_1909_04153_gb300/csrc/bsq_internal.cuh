@@ -87,6 +87,17 @@ struct Dev {
     Coef *coef;
 };
 
+// Block tables of a batched step: entry b of a stage's table says which
+// domain block b of that stage's single launch works on, and where (the
+// meaning of the remaining fields is the stage's, see the batched kernels).
+struct BatchPlan {
+    int n;                                        // domains
+    int nb_ghost, nb_rhs, nb_ysum, nb_yscan, nb_x;  // blocks of each stage's launch
+    const int4 *t_ghost, *t_rhs, *t_ysum, *t_yscan, *t_x;
+    int rhs_fast, rhs_theta1;                     // RHS variant shared by all domains
+    int yrow_max;                                 // x-solver shared row length (elements)
+};
+
 template <typename T>
 __host__ __device__ inline long long fidx(const Dev<T> &D, int i, int j)
 {

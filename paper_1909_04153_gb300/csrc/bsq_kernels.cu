@@ -195,11 +195,11 @@ __global__ void k_prologue(Dev<T> D, double forced_dt)
 // this block's atomicMax of the rate): the Eq. 22 rate of the new state is then
 // complete, so the controller of the next step runs here.
 template <typename T>
-__device__ void next_step_controller(const Dev<T> &D, double forced_dt_next)
+__device__ void next_step_controller(const Dev<T> &D, double forced_dt_next, unsigned nparts)
 {
     __threadfence();
     const unsigned ticket = atomicAdd(&D.ctl->done_count, 1u);
-    if (ticket == gridDim.x - 1) {
+    if (ticket == nparts - 1) {
         __threadfence();
         Coef cf;
         unsigned err;
@@ -269,7 +269,7 @@ __device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t,
 // Ghost fill at t_n + maker corrections of the line systems (the controller of
 // this step ran at the end of the previous step, or in the prologue).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
+__device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, long long stride)
 {
     const Coef scf = *D.coef;
     if (!scf.active) return;
@@ -278,8 +278,7 @@ __global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
     T *w = D.w[scf.wc];
     long long nghost = 4LL * ny + 4LL * (nx + 4);
     long long ntot = nghost + 2LL * ny + 2LL * nx;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot;
-         idx += (long long)gridDim.x * blockDim.x) {
+    for (long long idx = first; idx < ntot; idx += stride) {
         if (idx < 4LL * ny) {
             int side = (int)(idx / (2 * ny));
             int rem = (int)(idx % (2 * ny));
@@ -342,6 +341,12 @@ __global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
+{
+    ghost_body(D, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 // Ghost layers of Q at t_{n+1} (after the y-line solves), for F*(Q^{n+1}).
@@ -708,12 +713,12 @@ constexpr int SW_COLS = 28;  // interior columns per warp strip (lanes 2..29)
 // both history levels always read (they hold zeros, weighted by zero, during
 // the Euler start) and 32-bit offsets into the fields.
 template <typename T, int ROWS, bool THETA1, bool FAST>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
+__device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
     const int lane = threadIdx.x & 31;
-    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wg = blk * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int strip = wg % nstrip, band = wg / nstrip;
     const int nx = D.nx, ny = D.ny;
     const int j0 = band * ROWS;
@@ -956,7 +961,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
     // positivity clamps: warp total, one atomic per warp
     for (int o = 16; o > 0; o >>= 1) nclamp += __shfl_xor_sync(0xffffffffu, nclamp, o);
     if (lane == 0 && nclamp) atomicAdd(&D.ctl->clamps, nclamp);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blk == 0 && threadIdx.x == 0) {
         // commit the step in the controller state (the controller kernel of
         // this step has finished; no thread of this kernel reads Ctl)
         Ctl *ct = D.ctl;
@@ -967,6 +972,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
         ct->n = cf.n + 1;
         ct->rate_bits = 0ull;
     }
+}
+
+template <typename T, int ROWS, bool THETA1, bool FAST>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
+{
+    rhs_sw_body<T, ROWS, THETA1, FAST>(D, blockIdx.x, nstrip);
 }
 
 // ------------------------------------------------------------------ y-line solves
@@ -1081,12 +1092,12 @@ __global__ void __launch_bounds__(512, 2) k_ysolve(Dev<T> D, int CW, int NCH)
 // No thread waits on another inside a kernel; all accesses are coalesced
 // across 32 columns.
 template <typename T, int KY>
-__global__ void __launch_bounds__(256) k_ysum(Dev<T> D, int nch, T *sums)
+__device__ __forceinline__ void ysum_body(const Dev<T> &D, int bx, int by, int nch, T *sums)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = bx * 32 + threadIdx.x;
+    const int k = by * blockDim.y + threadIdx.y;
     const int nx = D.nx, ny = D.ny;
     if (i >= nx || k >= nch) return;
     const int j0 = k * KY;
@@ -1121,12 +1132,18 @@ __global__ void __launch_bounds__(256) k_ysum(Dev<T> D, int nch, T *sums)
     sums[4 * s + o] = be;
 }
 
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_ysum(Dev<T> D, int nch, T *sums)
+{
+    ysum_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, sums);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums, T *yin, T *xaft)
+__device__ __forceinline__ void yscan_body(const Dev<T> &D, int blk, int nch, const T *sums, T *yin, T *xaft)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
-    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int i = (int)((blk * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     const int nx = D.nx;
     if (i >= nx) return;
@@ -1191,13 +1208,19 @@ __global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums,
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_yscan(Dev<T> D, int nch, const T *sums, T *yin, T *xaft)
+{
+    yscan_body<T>(D, blockIdx.x, nch, sums, yin, xaft);
+}
+
 template <typename T, int KY>
-__global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
+__device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int nch, const T *yin, const T *xaft)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = bx * 32 + threadIdx.x;
+    const int k = by * blockDim.y + threadIdx.y;
     const int nx = D.nx, ny = D.ny;
     if (i >= nx || k >= nch) return;
     const int j0 = k * KY;
@@ -1257,6 +1280,12 @@ __global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin,
             if (D.kahan) D.cQ[o] = cq[q];
         }
     }
+}
+
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
+{
+    yapply_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, yin, xaft);
 }
 
 // ------------------------------------------------------------------ x-line solves
@@ -1505,7 +1534,7 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         }
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, forced_dt_next);
+        next_step_controller(D, forced_dt_next, gridDim.x);
     }
 }
 
@@ -1615,7 +1644,7 @@ __global__ void __launch_bounds__(512) k_xsolve_tma(Dev<T> D, int span, double f
         mbar_wait_bounded(&bar, 0, 1LL << 24);
         if (t == 0) {
             atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
-            next_step_controller(D, 0.0);
+            next_step_controller(D, 0.0, gridDim.x);
         }
         return;
     }
@@ -1819,7 +1848,7 @@ __global__ void __launch_bounds__(512) k_xsolve_tma(Dev<T> D, int span, double f
         }
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, forced_dt_next);
+        next_step_controller(D, forced_dt_next, gridDim.x);
     }
 }
 
@@ -2057,7 +2086,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         mbar_wait_bounded(&bar[1], 0, 1LL << 22);
         if (t == 0) {
             atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
-            next_step_controller(D, 0.0);
+            next_step_controller(D, 0.0, gridDim.x);
         }
         return;
     }
@@ -2076,7 +2105,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         }
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, forced_dt_next);
+        next_step_controller(D, forced_dt_next, gridDim.x);
     }
 }
 
@@ -2356,8 +2385,231 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_grp(Dev<T> D, int span, doubl
         if (anyfailed) atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, anyfailed ? 0.0 : forced_dt_next);
+        next_step_controller(D, anyfailed ? 0.0 : forced_dt_next, gridDim.x);
     }
+}
+
+// ---- one warp per x-line
+//
+// A warp solves row j in chunks of 32 K elements (lane l owns the K
+// contiguous elements c0 + l K ...).  Forward elimination runs over the chunks
+// left to right: local composition, a warp scan of the affine maps and the
+// carry y entering the chunk; the y values go to the warp's shared-memory
+// row.  Back substitution runs right to left with the carry x after the chunk
+// and finishes each chunk at once: compensated P update, sponge on w and P,
+// Eq. 22 rate.  Warps never wait on each other, so every row of the grid can
+// be in flight at once.  Same arithmetic as k_xsolve.
+template <typename T, int K>
+__device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf, int j, T *ys, T &rate, bool &bad)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = D.nx, ny = D.ny;
+    const bool seq = D.cross_mode != 0;
+    const long long rowo = fidx(D, 0, j);
+    const T *Qr = D.Q + rowo, *br = D.bC + rowo;
+    const T corrW = D.corrW[j], corrE = D.corrE[j];
+    const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+    const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+    T carry = (T)0;
+    int c0 = 0;
+    for (; c0 < nx; c0 += 32 * K) {
+        const int ib = c0 + lane * K;
+        T r[K], m[K], e[K];
+        vload_k<T, K>(D.dU + rowo + ib, r);
+        vload_k<T, K>(D.fxm + rowo + ib, m);
+        vload_k<T, K>(D.fxe + rowo + ib, e);
+        if (seq) {
+            T Qc[K + 2], bc_[K + 2], qm[K + 2], qp[K + 2], bm[K], bp[K];
+            load_halo_chunk<T, K>(Qr, ib, lane, Qc);
+            load_halo_chunk<T, K>(br, ib, lane, bc_);
+            load_halo_chunk<T, K>(Qr - D.pitch, ib, lane, qm);
+            load_halo_chunk<T, K>(Qr + D.pitch, ib, lane, qp);
+            vload_k<T, K>(br - D.pitch + ib, bm);
+            vload_k<T, K>(br + D.pitch + ib, bp);
+            // ghosts of Q^{n+1} at t_{n+1}, as in k_xsolve_pipe
+            if (ib == 0) {
+                if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
+                Qc[0] = D.bc[SW] == MAKER ? D.mqW[j] : Qc[1];
+                if (j + 1 < ny) qp[0] = D.bc[SW] == MAKER ? D.mqW[j + 1] : qp[1];
+            }
+            if (nx - 1 >= ib && nx - 1 < ib + K) {
+                const int qe = nx - ib;
+#pragma unroll
+                for (int q = 1; q <= K; q++)
+                    if (q == qe) {
+                        if (j - 1 >= 0) qm[q + 1] = D.bc[SE] == MAKER ? D.mqE[j - 1] : qm[q];
+                        Qc[q + 1] = D.bc[SE] == MAKER ? D.mqE[j] : Qc[q];
+                        if (j + 1 < ny) qp[q + 1] = D.bc[SE] == MAKER ? D.mqE[j + 1] : qp[q];
+                    }
+            }
+            if (j == 0 || j == ny - 1) {
+                const int side = j == 0 ? SS : SN;
+                const T *mq = side == SS ? D.mqS : D.mqN;
+#pragma unroll
+                for (int q = 0; q < K + 2; q++) {
+                    const int cc = ib - 1 + q;
+                    const T gv = D.bc[side] == MAKER ? mq[min(max(cc, -1), nx) + 1] : -Qc[q];
+                    if (j == 0) qm[q] = gv;
+                    else qp[q] = gv;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                T d = tmax(D.w_s - bc_[q + 1], (T)0);
+                T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
+                T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
+                T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
+                T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+                T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const int i = ib + q;
+            if (i == 0) r[q] += corrW;
+            if (i == nx - 1) r[q] += corrE;
+            if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
+        }
+        T A = (T)1, B = (T)0;
+#pragma unroll
+        for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T Ap = __shfl_up_sync(0xffffffffu, A, o);
+            T Bp = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+        }
+        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) { Ae = (T)1; Be = (T)0; }
+        T y = Ae * carry + Be;
+#pragma unroll
+        for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = y; }
+        vstore_k<T, K>(ys + ib, r);
+        carry = __shfl_sync(0xffffffffu, y, 31);
+    }
+    __syncwarp();
+    // back substitution, last chunk first
+    carry = (T)0;
+    const T gyj = D.gy[j];
+    T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo;
+    T *wrow = D.w[cf.wc ^ 1] + rowo;
+    for (c0 -= 32 * K; c0 >= 0; c0 -= 32 * K) {
+        const int ib = c0 + lane * K;
+        T x[K], c[K], Pv[K], cPv[K], wv[K], Qv[K], bv[K], gxv[K];
+        vload_k<T, K>(ys + ib, x);
+        vload_k<T, K>(D.gx + ib, gxv);
+        vload_k<T, K>(D.fxc + rowo + ib, c);
+        vload_k<T, K>(Pr + ib, Pv);
+        if (D.kahan) vload_k<T, K>(cPr + ib, cPv);
+        vload_k<T, K>(wrow + ib, wv);
+        vload_k<T, K>(Qr + ib, Qv);
+        vload_k<T, K>(br + ib, bv);
+#pragma unroll
+        for (int q = 0; q < K; q++)
+            if (ib + q >= nx) { c[q] = (T)0; x[q] = (T)0; }
+        T al = (T)0, be = (T)1;
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { al = x[q] - c[q] * al; be = -c[q] * be; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, al, o);
+            T bp = __shfl_down_sync(0xffffffffu, be, o);
+            if (lane + o < 32) { al = al + be * ap; be = be * bp; }
+        }
+        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
+        if (lane == 31) { an = (T)0; bn = (T)1; }
+        T xx = an + bn * carry;
+#pragma unroll
+        for (int q = K - 1; q >= 0; q--) { xx = x[q] - c[q] * xx; x[q] = xx; }
+        carry = __shfl_sync(0xffffffffu, xx, 0);
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const int i = ib + q;
+            if (i >= nx) continue;
+            T Pn, cn = (T)0;
+            if (D.kahan) {
+                T yy = x[q] - cPv[q];
+                Pn = Pv[q] + yy;
+                cn = (Pn - Pv[q]) - yy;
+            } else {
+                Pn = Pv[q] + x[q];
+            }
+            T wq = wv[q];
+            T gm = gxv[q] * gyj;
+            if (gm < (T)1) {
+                T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
+                wq = bv[q] + (d + gm * (h - d));
+                wrow[i] = wq;
+                if (D.kahan) cwr[i] = (T)0;
+                Pn *= gm;
+                cn *= gm;
+            }
+            Pv[q] = Pn;
+            cPv[q] = cn;
+            T h = tmax(wq - bv[q], (T)0);
+            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
+            T u = iv * Pn, v = iv * Qv[q];
+            T cc = tsqrt(D.g * h);
+            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+        }
+        if (ib < nx) {
+            vstore_k<T, K>(Pr + ib, Pv);
+            if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+        }
+    }
+}
+
+constexpr int XW_WARPS = 4;  // rows (warps) per block of the warp-per-row x-solver
+
+// shared memory of the warp-per-row x-solver: one y row per warp
+template <typename T, int K>
+static size_t xwarp_smem(int nx)
+{
+    const int span = 32 * K;
+    return (size_t)XW_WARPS * (size_t)((nx + span - 1) / span) * span * sizeof(T);
+}
+
+// rows blk * XW_WARPS + warp of one domain; the controller of the domain's
+// next step runs in the last of its nparts blocks
+template <typename T, int K>
+__device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsigned nparts, int yrow,
+                                                 double forced_dt_next)
+{
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double smax[XW_WARPS];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *ys = reinterpret_cast<T *>(smem_raw) + (size_t)wid * yrow;
+    const int j = blk * XW_WARPS + wid;
+    T rate = (T)0;
+    bool bad = false;
+    if (j < D.ny) xsolve_row_warp<T, K>(D, cf, j, ys, rate, bad);
+    double rr = (double)rate;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        bool fl = false;
+        for (int q = 0; q < XW_WARPS; q++) {
+            if (smax[q] < 0.0) fl = true;
+            else mx = fmax(mx, smax[q]);
+        }
+        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
+        atomicMax(&D.ctl->rate_bits, dbits(mx));
+        next_step_controller(D, forced_dt_next, nparts);
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(32 * XW_WARPS) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
+{
+    xsolve_warp_body<T, K>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
 }
 
 // shared memory bytes of the TMA x-solver for a row span
@@ -2532,6 +2784,10 @@ cudaError_t configure(int nx)
         e = cudaFuncSetAttribute(k_xsolve_grp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_grp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_warp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_warp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     return e;
 }
 
@@ -2552,6 +2808,13 @@ template <typename T>
 static bool xsolver_staging_allowed(const Dev<T> &D)
 {
     return D.tune_xtma == 0 || D.tune_xtma == 3;
+}
+// the warp-per-row x-solver (tune_xtma 4), K = 4 or 8, y row in shared memory
+template <typename T>
+static bool xsolver_warp(const Dev<T> &D, int nx)
+{
+    const int K = x_chunk<T>(nx, D.tune_xk);
+    return D.tune_xtma == 4 && (K == 4 || K == 8) && (K == 4 ? xwarp_smem<T, 4>(nx) : xwarp_smem<T, 8>(nx)) <= 96 * 1024;
 }
 
 // One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
@@ -2620,15 +2883,25 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
-    const bool grp = xsolver_grouped(D, nx);
+    const bool xwarp = xsolver_warp(D, nx);
+    const bool grp = !xwarp && xsolver_grouped(D, nx);
     const bool pipe = !grp && xsolver_staging_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM;
-    const bool tma = grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
+    const bool tma = xwarp || grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
     if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (grp) {
+    if (xwarp) {
+        const int xb = (ny + XW_WARPS - 1) / XW_WARPS;
+        if (K == 4) {
+            const int yrow = (nx + 127) / 128 * 128;
+            k_xsolve_warp<T, 4><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
+        } else {
+            const int yrow = (nx + 255) / 256 * 256;
+            k_xsolve_warp<T, 8><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
+        }
+    } else if (grp) {
         const int grid = min((ny + 1) / 2, D.nsm);
         const size_t gs = 2 * xgrp_smem<T>(span, D.hx);
         if (K == 4) k_xsolve_grp<T, 4><<<grid, 2 * thr, gs, st>>>(D, span, forced_dt_next);
@@ -2659,7 +2932,7 @@ int xsolver_staged(const Dev<T> &D, int nx)
     const int K = x_chunk<T>(nx, D.tune_xk);
     const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const size_t xs = xtma_smem<T>(thr * K, D.hx);
-    return xsolver_grouped(D, nx) || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
+    return xsolver_warp(D, nx) || xsolver_grouped(D, nx) || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
 }
 
 template <typename T>
@@ -2712,6 +2985,153 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ batched step
+//
+// Many domains advance together: each stage is one launch over the blocks of
+// all domains, and a per-stage block table gives every block its domain and
+// its block coordinates inside that domain.  A block copies its domain's
+// descriptor into shared memory and runs the same body as the single-domain
+// kernel.  A domain whose controller has stopped it (t_end or step limit
+// reached, or an error) has an inactive Coef: its blocks return at once.
+
+// copy domain `dom`'s descriptor to shared memory (all threads of the block)
+template <typename T>
+__device__ __forceinline__ const Dev<T> &batch_dev(const Dev<T> *Ds, int dom)
+{
+    __shared__ __align__(16) unsigned long long sdev[(sizeof(Dev<T>) + 7) / 8];
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(Ds + dom);
+    const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int q = tid; q < (int)(sizeof(Dev<T>) / 8); q += nthr) sdev[q] = src[q];
+    __syncthreads();
+    return *reinterpret_cast<const Dev<T> *>(sdev);
+}
+
+// table entry: (domain, block of that domain, that domain's block count, 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    ghost_body(D, (long long)e.y * blockDim.x + threadIdx.x, (long long)e.z * blockDim.x);
+}
+
+// table entry: (domain, block of that domain, strips of 28 columns, 0)
+template <typename T, int ROWS, bool THETA1, bool FAST>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    rhs_sw_body<T, ROWS, THETA1, FAST>(D, e.y, e.z);
+}
+
+// table entry: (domain, column group, chunk group, chunks per column)
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_ysum_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    ysum_body<T, KY>(D, e.y, e.z, e.w, D.ysums);
+}
+
+// table entry: (domain, block of that domain, chunks per column, 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_yscan_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    yscan_body<T>(D, e.y, e.z, D.ysums, D.yin, D.yxa);
+}
+
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_yapply_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    yapply_body<T, KY>(D, e.y, e.z, e.w, D.yin, D.yxa);
+}
+
+// table entry: (domain, block of that domain, that domain's block count,
+// shared row length of the domain)
+template <typename T, int K>
+__global__ void __launch_bounds__(32 * XW_WARPS) k_xsolve_warp_b(const Dev<T> *Ds, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    const Dev<T> &D = batch_dev(Ds, e.x);
+    xsolve_warp_body<T, K>(D, e.y, (unsigned)e.z, e.w, 0.0);
+}
+
+// limits of the run and the controller of the first step, one thread per domain
+template <typename T>
+__global__ void k_batch_start(const Dev<T> *Ds, int n, const double *t_end, long long max_steps)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n) return;
+    const Dev<T> &D = Ds[d];
+    Ctl *ctl = D.ctl;
+    ctl->t_end = t_end[d];
+    ctl->n_limit = max_steps > 0 ? ctl->n + max_steps : 0x7fffffffffffffffLL;
+    Coef cf;
+    unsigned err;
+    controller(D, 0.0, cf, err);
+    *D.coef = cf;
+    if (err) atomicOr(&ctl->err, err);
+    ctl->done_count = 0u;
+}
+
+template <typename T>
+__global__ void k_batch_gather(const Dev<T> *Ds, int n, Ctl *out)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < n) out[d] = *Ds[d].ctl;
+}
+
+// x-solver elements per thread of a batch (the default x_chunk, which also
+// set every member's row pitch)
+template <typename T>
+int batch_xchunk()
+{
+    return sizeof(T) == 4 ? 8 : 4;
+}
+
+template <typename T>
+cudaError_t configure_batch(int yrow_max)
+{
+    const int bytes = XW_WARPS * yrow_max * (int)sizeof(T);
+    if (batch_xchunk<T>() == 8)
+        return cudaFuncSetAttribute(k_xsolve_warp_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_xsolve_warp_b<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T>
+cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
+{
+    k_ghost_b<T><<<P.nb_ghost, 256, 0, st>>>(Ds, P.t_ghost);
+    if (P.rhs_fast) k_rhs_sw_b<T, 64, true, true><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    else if (P.rhs_theta1) k_rhs_sw_b<T, 64, true, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    else k_rhs_sw_b<T, 64, false, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    k_ysum_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    k_yscan_b<T><<<P.nb_yscan, 256, 0, st>>>(Ds, P.t_yscan);
+    k_yapply_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    const size_t xs = (size_t)XW_WARPS * P.yrow_max * sizeof(T);
+    if (batch_xchunk<T>() == 8) k_xsolve_warp_b<T, 8><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
+    else k_xsolve_warp_b<T, 4><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_start(const Dev<T> *Ds, int n, const double *t_end, long long max_steps, cudaStream_t st)
+{
+    k_batch_start<T><<<(n + 63) / 64, 64, 0, st>>>(Ds, n, t_end, max_steps);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t st)
+{
+    k_batch_gather<T><<<(n + 63) / 64, 64, 0, st>>>(Ds, n, out);
+    return cudaGetLastError();
+}
+
 #define BSQ_INST(T)                                                                              \
     template int step_shape_ok<T>(int, int);                                                     \
     template int row_pitch<T>(int, int);                                                         \
@@ -2722,6 +3142,11 @@ cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
     template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
     template int xsolver_staged<T>(const Dev<T> &, int);                                         \
+    template int batch_xchunk<T>();                                                              \
+    template cudaError_t configure_batch<T>(int);                                                \
+    template cudaError_t launch_batch_step<T>(const Dev<T> *, const BatchPlan &, cudaStream_t);  \
+    template cudaError_t launch_batch_start<T>(const Dev<T> *, int, const double *, long long, cudaStream_t); \
+    template cudaError_t launch_batch_gather<T>(const Dev<T> *, int, Ctl *, cudaStream_t);       \
     template cudaError_t launch_extract<T>(const Dev<T> &, cudaStream_t, int, int, T *);         \
     template cudaError_t launch_mass<T>(const Dev<T> &, cudaStream_t, int, double *, int);
 BSQ_INST(float)

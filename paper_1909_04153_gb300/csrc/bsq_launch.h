@@ -22,4 +22,12 @@ template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t s
 template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);
 cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long max_steps);
 
+// batched steps over many domains (one launch per stage)
+template <typename T> int batch_xchunk();
+template <typename T> cudaError_t configure_batch(int yrow_max);
+template <typename T> cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_batch_start(const Dev<T> *Ds, int n, const double *t_end, long long max_steps, cudaStream_t st);
+template <typename T> cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t st);
+
 }  // namespace bsq

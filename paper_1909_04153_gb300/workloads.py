@@ -164,6 +164,17 @@ def batch_sizes(count=64, lo=128, hi=1024, seed=SEED, multiple=32):
     return [int(max(multiple, round(v / multiple) * multiple)) for v in s]
 
 
+def batch_cases(count=64, lo=128, hi=1024, seed=SEED, dx=0.1, steps=1000, **kw):
+    """Independent square basins for batched runs: sides from batch_sizes, each
+    with its own seed, forcing drawn 50/50 (seeded) between a solitary wave and
+    a JONSWAP maker."""
+    rng = np.random.default_rng(seed + 7)
+    sides = batch_sizes(count, lo, hi, seed)
+    kinds = rng.integers(0, 2, size=count)
+    return [random_basin(n, dx=dx, seed=seed + 100 + q, forcing="solitary" if kinds[q] == 0 else "jonswap",
+                         steps=steps, **kw) for q, n in enumerate(sides)]
+
+
 CASES = {
     "solitary_basin": solitary_basin,
     "planar_beach": planar_beach,

@@ -1,0 +1,148 @@
+"""Batched domains (bsq_batch_*): many uneven domains, one launch per stage,
+each with its own adaptive dt.
+
+* Each member's result in the mix is bitwise the result of the same domain
+  run alone through the batched path (a batch of one), in FP32 and FP64, with
+  a common step limit and with per-member t_end.
+* Against the same domain on the single-domain path (other kernel shapes, so
+  other rounding order): the same number of steps and the stated tolerances
+  (FP64 1e-10, FP32 1e-4 relative L2 in eta).
+* An FP64 member follows the oracle's adaptive dt trace.
+* A failing member (non-finite state) stops alone; the others finish and are
+  unchanged by it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_04153_gb300 import bsq
+from paper_1909_04153_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    # uneven shapes, ragged tails, both forcings, walls / makers / sponges
+    return [
+        W.random_basin(96, seed=11, forcing="solitary"),
+        W.random_basin(160, seed=12, forcing="jonswap"),
+        W.barred_beach(nx=130, ny=70),
+        W.random_basin(64, seed=13, forcing="jonswap"),
+        W.solitary_basin(nx=200, ny=9, dx=0.1),
+    ]
+
+
+def _fields(d):
+    return {f: d.read(f) for f in ("eta", "P", "Q")}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _alone(case, prec, **kw):
+    """The domain run alone through the batched path (a batch of one)."""
+    d = bsq.Domain(case, precision=prec, graph_steps=8)
+    with bsq.Batch([d]) as b:
+        n = b.advance(**kw)
+    return d, int(n[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_members_equal_alone_bitwise(prec):
+    cases = _members()
+    steps = 70
+    doms = [bsq.Domain(c, precision=prec, graph_steps=8) for c in cases]
+    with bsq.Batch(doms) as b:
+        done = b.advance(max_steps=steps)
+    assert list(done) == [steps] * len(cases)
+    for c, d in zip(cases, doms):
+        s, n = _alone(c, prec, max_steps=steps)
+        assert n == steps
+        i1, i2 = d.info(), s.info()
+        assert i1["n"] == i2["n"] and i1["t"] == i2["t"] and i1["clamps"] == i2["clamps"]
+        for k in ("eta", "P", "Q"):
+            np.testing.assert_array_equal(d.read(k), s.read(k))
+        # the single-domain path: same steps, other rounding order
+        with bsq.Domain(c, precision=prec) as u:
+            u.advance(max_steps=steps)
+            tol = 1e-10 if prec == "fp64" else 1e-4
+            assert abs(u.info()["t"] - i1["t"]) <= (1e-12 if prec == "fp64" else 1e-6) * i1["t"]
+            assert rel(d.read("eta"), u.read("eta")) <= tol
+        s.close()
+        d.close()
+
+
+def test_batch_per_member_t_end():
+    cases = _members()[:4]
+    t_end = [0.05, 0.11, 0.07, 0.13]
+    doms = [bsq.Domain(c, precision="fp32", graph_steps=8) for c in cases]
+    with bsq.Batch(doms) as b:
+        done = b.advance(t_end=t_end)
+    for c, d, te, nd in zip(cases, doms, t_end, done):
+        info = d.info()
+        assert abs(info["t"] - te) <= 1e-12 * max(1.0, te)
+        assert info["n"] == nd
+        s, n = _alone(c, "fp32", t_end=[te])
+        assert n == nd
+        np.testing.assert_array_equal(s.read("eta"), d.read("eta"))
+        s.close()
+        d.close()
+
+
+def test_batch_member_follows_oracle_dt_trace():
+    case = W.random_basin(72, seed=21, forcing="jonswap")
+    other = W.random_basin(40, seed=22, forcing="solitary")
+    o = oracle.OracleDomain(case["params"], case["bed"], case["comps"], case["eta0"], case["P0"], case["Q0"])
+    ref = []
+    for _ in range(60):
+        o.step()
+        ref.append(o.info()["last_dt"])
+    a = bsq.Domain(case, precision="fp64", graph_steps=4)
+    z = bsq.Domain(other, precision="fp64", graph_steps=4)
+    got = []
+    with bsq.Batch([z, a]) as b:
+        for _ in range(60):
+            b.advance(max_steps=1)
+            got.append(a.info()["last_dt"])
+    np.testing.assert_allclose(got, ref, rtol=1e-8)
+    e = a.read("eta")
+    assert np.linalg.norm(e - o.get("eta")) <= 1e-8 * np.linalg.norm(o.get("eta"))
+    a.close()
+    z.close()
+
+
+def test_failing_member_stops_alone():
+    cases = _members()[:3]
+    bad = dict(cases[1])
+    P0 = np.zeros((bad["params"]["ny"], bad["params"]["nx"]))
+    P0[5, 7] = np.nan
+    bad["P0"] = P0
+    doms = [bsq.Domain(cases[0], precision="fp32", graph_steps=8), bsq.Domain(bad, precision="fp32", graph_steps=8),
+            bsq.Domain(cases[2], precision="fp32", graph_steps=8)]
+    with bsq.Batch(doms) as b:
+        with pytest.raises(bsq.BsqError) as ei:
+            b.advance(max_steps=40)
+        assert ei.value.status == bsq.ERR_NONFINITE
+    assert doms[0].info()["n"] == 40 and doms[2].info()["n"] == 40
+    for q in (0, 2):
+        s, n = _alone(cases[q], "fp32", max_steps=40)
+        np.testing.assert_array_equal(s.read("eta"), doms[q].read("eta"))
+        s.close()
+    with pytest.raises(bsq.BsqError):  # sticky on the failed member
+        doms[1].advance(max_steps=1)
+    for d in doms:
+        d.close()
+
+
+def test_batch_rejects_mixed_precision_and_repeats():
+    c = W.random_basin(48, seed=3)
+    a = bsq.Domain(c, precision="fp32")
+    z = bsq.Domain(c, precision="fp64")
+    with pytest.raises(bsq.BsqError) as ei:
+        bsq.Batch([a, z])
+    assert ei.value.status == bsq.ERR_ARG
+    with pytest.raises(bsq.BsqError):
+        bsq.Batch([a, a])
+    a.close()
+    z.close()
