@@ -303,6 +303,13 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": eta.nbytes / args.steps,
            "includes": "bsq_create from host arrays + bsq_advance + bsq_read(eta)"}
 
+    batched = None
+    if rank == 0 and prec == "fp32" and not args.no_batched:
+        batched = run_batched(args, dev, stream)
+    served = None
+    if rank == 0 and prec == "fp32" and not args.no_served:
+        served = run_served(args, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # bounded sample: the same layout on a 256 x 256 grid, ~15 s of oracle work
@@ -333,6 +340,8 @@ def run_ours(args):
             "gpu_launches": launches * args.graph_steps * math.ceil(args.steps / args.graph_steps) + 2,
             "launches_per_step": launches,
             "fp64": fp64,
+            "batched": batched,
+            "served": served,
             "clocks": clocks,
             "sim": {"t": info["t"], "clamps": info["clamps"]},
         }
@@ -341,6 +350,142 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return 0
+
+
+def run_batched(args, dev, stream):
+    """64 independent FP32 basins (sides log-uniform in [128, 1024], multiples
+    of 32) advanced as one batch, each with its own adaptive dt; beside it the
+    same domains advanced one at a time on the single-domain path, in FP32
+    and in FP64."""
+    import torch
+
+    from paper_1909_04153_gb300 import bsq
+
+    cases = W.batch_cases(args.batch_domains, 128, 1024)
+    cells = [c["params"]["nx"] * c["params"]["ny"] for c in cases]
+    total = float(sum(cells))
+    doms = [bsq.Domain(c, precision="fp32", stream=stream.cuda_stream, graph_steps=args.graph_steps)
+            for c in cases]
+    batch = bsq.Batch(doms, stream=stream.cuda_stream)
+    batch.advance(max_steps=10)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    done = batch.advance(max_steps=args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    if not all(int(n) == args.batch_steps for n in done):
+        raise RuntimeError("batched run: steps %s" % list(done))
+    value = total * args.batch_steps / (ms * 1e-3)
+    launches = batch.launches_per_step()
+    batch.close()
+
+    def one_at_a_time(ds, steps):
+        el = 0.0
+        for d in ds:
+            d.advance(max_steps=2)
+            torch.cuda.synchronize(dev)
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            d.advance(max_steps=steps)
+            z.record(stream)
+            torch.cuda.synchronize(dev)
+            el += a.elapsed_time(z) * 1e-3
+        return total * steps / el
+
+    v32 = one_at_a_time(doms, args.batch_solo_steps)
+    for d in doms:
+        d.close()
+    d64 = [bsq.Domain(c, precision="fp64", stream=stream.cuda_stream, graph_steps=args.graph_steps)
+           for c in cases]
+    v64 = one_at_a_time(d64, args.batch_fp64_steps)
+    for d in d64:
+        d.close()
+    return {
+        "workload": "%d random basins, sides log-uniform 128-1024 (multiples of 32), dx 0.1 m, depth 0.2-2 m, "
+                    "solitary or JONSWAP maker (seeded 50/50)" % len(cases),
+        "domains": len(cases), "cells": int(total), "precision": "fp32", "kahan": True,
+        "value": value, "unit": "cell-updates/s", "ms_per_step": ms / args.batch_steps,
+        "steps": args.batch_steps, "launches_per_step": launches,
+        "gpu_launches": launches * args.graph_steps * math.ceil(args.batch_steps / args.graph_steps) + 1,
+        "one_at_a_time_fp32": {"value": v32, "unit": "cell-updates/s", "steps_each": args.batch_solo_steps},
+        "one_at_a_time_fp64": {"value": v64, "unit": "cell-updates/s", "steps_each": args.batch_fp64_steps},
+        "speedup_vs_fp64_one_at_a_time": value / v64,
+        "speedup_vs_fp32_one_at_a_time": value / v32,
+    }
+
+
+def run_served(args, dev, stream):
+    """A seeded Poisson stream of FP32 simulation requests (mean 20 per second,
+    sides log-uniform in [64, 2048], multiples of 32, simulated durations
+    uniform in [5, 60] s times --serve-time-scale, inputs as the batched
+    basins), served with continuous batching under a device-memory budget;
+    time-to-result is taken from each request's arrival to its result on the
+    host."""
+    import torch
+
+    from paper_1909_04153_gb300 import bsq
+
+    n = args.serve_requests
+    rng = np.random.default_rng(W.SEED + 5)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sides = [int(max(32, round(v / 32) * 32)) for v in np.exp(rng.uniform(math.log(64), math.log(2048), size=n))]
+    durations = rng.uniform(5.0, 60.0, size=n) * args.serve_time_scale
+    kinds = rng.integers(0, 2, size=n)
+    cases = [W.random_basin(s, seed=W.SEED + 500 + q, forcing="solitary" if kinds[q] == 0 else "jonswap")
+             for q, s in enumerate(sides)]
+    budget = int(args.serve_budget_gb * 1e9)
+    srv = bsq.Server(hbm_budget=budget, max_slots=args.serve_slots, steps_per_round=args.serve_round,
+                     stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    submitted, ids, done_at, steps, failed = 0, {}, {}, {}, 0
+    h2d = d2h = 0
+    max_running = 0
+    while len(done_at) < n:
+        now = time.perf_counter() - t0
+        while submitted < n and arrivals[submitted] <= now:
+            rid = srv.submit(cases[submitted], float(durations[submitted]))
+            ids[rid] = submitted
+            c = cases[submitted]
+            h2d += 8 * ((c["params"]["nx"] + 1) * (c["params"]["ny"] + 1)
+                        + sum(c[k].size for k in ("eta0", "P0", "Q0") if c.get(k) is not None))
+            submitted += 1
+        nr, npd = srv.poll()
+        max_running = max(max_running, nr)
+        for rid, q in list(ids.items()):
+            r = srv.request(rid)
+            if r["state"] in (bsq.REQ_DONE, bsq.REQ_FAILED):
+                if r["state"] == bsq.REQ_DONE:
+                    eta = srv.read(rid, "eta")
+                    d2h += eta.nbytes
+                else:
+                    failed += 1
+                done_at[q] = time.perf_counter() - t0
+                steps[q] = r["steps"]
+                srv.release(rid)
+                del ids[rid]
+        if nr == 0 and npd == 0 and submitted < n:
+            time.sleep(max(0.0, arrivals[submitted] - (time.perf_counter() - t0)))
+    srv.close()
+    lat = np.array([done_at[q] - arrivals[q] for q in range(n)])
+    work = float(sum(sides[q] * sides[q] * steps[q] for q in range(n)))
+    makespan = max(done_at.values()) - arrivals[0]
+    return {
+        "workload": "%d requests, Poisson arrivals %.0f/s, sides log-uniform 64-2048 (multiples of 32), "
+                    "simulated durations U[5, 60] s x %g, random basins (solitary or JONSWAP maker)" % (
+                        n, args.serve_rate, args.serve_time_scale),
+        "precision": "fp32", "hbm_budget_bytes": budget, "max_slots": args.serve_slots,
+        "steps_per_round": args.serve_round,
+        "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        "mean_s": float(lat.mean()),
+        "value": work / makespan, "unit": "cell-updates/s",
+        "offered": work / max(arrivals[-1] - arrivals[0], 1e-9),
+        "makespan_s": makespan, "cell_updates": work, "failed": failed, "max_running": max_running,
+        "e2e_bytes": {"h2d": h2d, "d2h": d2h},
+    }
 
 
 def bsq_bytes_estimate(ncell, fp):
@@ -361,6 +506,18 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=40)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-time-scale", type=float, default=0.1)
+    ap.add_argument("--serve-budget-gb", type=float, default=4.0)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-round", type=int, default=32)
+    ap.add_argument("--batch-domains", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-solo-steps", type=int, default=32)
+    ap.add_argument("--batch-fp64-steps", type=int, default=16)
     ap.add_argument("--tune", type=lambda s: tuple(int(v) for v in s.split(",")), default=None,
                     help="kernel shape knobs (bsq_params.tune), comma separated")
     args = ap.parse_args(argv)

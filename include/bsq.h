@@ -224,6 +224,77 @@ int bsq_batch_launches_per_step(const bsq_batch *b);
 /* Release the batch (not its domains); NULL-safe. */
 void bsq_batch_destroy(bsq_batch *b);
 
+/* Time and step count of the domain as of the end of its last advance call
+ * (bsq_advance, bsq_step_dt or bsq_batch_advance; 0 after bsq_create), from
+ * the host copy: no device work and no wait.  Returns the domain's status
+ * (its sticky error, or the error its last advance ended with). */
+bsq_status bsq_clock(const bsq_domain *d, double *t, long long *n);
+
+/* Device bytes bsq_create allocates for these parameters with n_comp wave-
+ * maker components (0 for sizes bsq_create rejects). */
+size_t bsq_domain_bytes(const bsq_params *p, int n_comp);
+
+/* ---- Serving: continuous batching of simulation requests.
+ *
+ * A request is a domain (same arguments as bsq_create) and an end time.
+ * Submitted requests wait in a first-come-first-served queue on the host; a
+ * poll admits requests while a slot is free and their device bytes
+ * (bsq_domain_bytes) fit the budget next to those held, rebuilds the batch
+ * when its membership changed, advances all running requests together by
+ * steps_per_round steps (each with its own adaptive dt, Eqs. 22, 47), and
+ * retires those that reached their end time.  A finished request keeps its
+ * device memory (and its share of the budget) until bsq_server_release.
+ * Every request's result is the same as when it is served alone.  One host
+ * thread drives a server; calls are not thread-safe. */
+typedef struct bsq_server bsq_server;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes all admitted requests may hold; 0: no limit */
+    int max_slots;        /* requests advanced together at most; <= 0: 64 */
+    int steps_per_round;  /* steps per bsq_server_poll; <= 0: 32 */
+    int precision;        /* BSQ_FP32 or BSQ_FP64: every request's precision */
+    int kahan;            /* FP32: every request's Kahan setting */
+    void *cuda_stream;    /* stream of every request and batch; NULL: library streams */
+} bsq_server_config;
+
+enum { BSQ_REQ_PENDING = 0, BSQ_REQ_RUNNING = 1, BSQ_REQ_DONE = 2, BSQ_REQ_FAILED = 3 };
+
+bsq_status bsq_server_create(const bsq_server_config *cfg, bsq_server **out);
+
+/* Queue a request; the inputs are copied (host memory until admission).
+ * Requests must use the server's precision and Kahan setting, the
+ * sequential cross form, default tune, ny <= 2048 and rows the batched
+ * x-solver holds; t_end > 0 finite; a request larger than the whole budget is
+ * refused (BSQ_ERR_ARG).  *id receives the request id (> 0). */
+bsq_status bsq_server_submit(bsq_server *s, const bsq_params *p, const double *bed_corners,
+                             const bsq_boundary *bnd, const double *eta0, const double *P0, const double *Q0,
+                             double t_end, long long *id);
+
+/* One round: admit, advance, retire.  n_running / n_pending (may be NULL)
+ * receive the counts after the round.  A request that fails (creation, or a
+ * non-finite state) is finished as BSQ_REQ_FAILED with its status; the call
+ * itself fails only for errors of the batch (BSQ_ERR_CUDA, BSQ_ERR_TIMEOUT). */
+bsq_status bsq_server_poll(bsq_server *s, int *n_running, int *n_pending);
+
+/* State (BSQ_REQ_*), simulated time and steps (as of the last poll) and
+ * status of a request.  BSQ_ERR_ARG for an unknown or released id. */
+bsq_status bsq_server_request(const bsq_server *s, long long id, int *state, double *t, long long *steps,
+                              int *status);
+
+/* Read a field of a finished request (as bsq_read); BSQ_ERR_STATE if it is
+ * not BSQ_REQ_DONE. */
+bsq_status bsq_server_read(const bsq_server *s, long long id, int field, double *host_out);
+
+/* Free a finished (or failed) request's device memory and forget it;
+ * BSQ_ERR_STATE while it is pending or running. */
+bsq_status bsq_server_release(bsq_server *s, long long id);
+
+/* Device bytes held by admitted, not yet released requests. */
+size_t bsq_server_bytes_in_use(const bsq_server *s);
+
+/* Release everything (queued requests, domains, the batch); NULL-safe. */
+void bsq_server_destroy(bsq_server *s);
+
 /* Allocation-free variant of the volume reduction that bsq_info's mass uses.
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc, such as an application that owns every byte of device memory

@@ -45,6 +45,16 @@ class bsq_boundary(ctypes.Structure):
     ]
 
 
+class bsq_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("steps_per_round", ctypes.c_int),
+        ("precision", ctypes.c_int), ("kahan", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+
+
 class BsqError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -102,6 +112,27 @@ def lib():
         L.bsq_batch_launches_per_step.restype = ctypes.c_int
         L.bsq_batch_launches_per_step.argtypes = [vp]
         L.bsq_batch_destroy.argtypes = [vp]
+        L.bsq_clock.restype = ctypes.c_int
+        L.bsq_clock.argtypes = [vp, _DP, ctypes.POINTER(ctypes.c_longlong)]
+        L.bsq_domain_bytes.restype = sz
+        L.bsq_domain_bytes.argtypes = [ctypes.POINTER(bsq_params), ctypes.c_int]
+        L.bsq_server_create.restype = ctypes.c_int
+        L.bsq_server_create.argtypes = [ctypes.POINTER(bsq_server_config), ctypes.POINTER(vp)]
+        L.bsq_server_submit.restype = ctypes.c_int
+        L.bsq_server_submit.argtypes = [vp, ctypes.POINTER(bsq_params), _DP, ctypes.POINTER(bsq_boundary), _DP, _DP,
+                                        _DP, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+        L.bsq_server_poll.restype = ctypes.c_int
+        L.bsq_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.bsq_server_request.restype = ctypes.c_int
+        L.bsq_server_request.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), _DP,
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
+        L.bsq_server_read.restype = ctypes.c_int
+        L.bsq_server_read.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, _DP]
+        L.bsq_server_release.restype = ctypes.c_int
+        L.bsq_server_release.argtypes = [vp, ctypes.c_longlong]
+        L.bsq_server_bytes_in_use.restype = sz
+        L.bsq_server_bytes_in_use.argtypes = [vp]
+        L.bsq_server_destroy.argtypes = [vp]
         L.bsq_mass_noalloc.restype = ctypes.c_int
         L.bsq_mass_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                        ctypes.c_double, ctypes.c_double, vp, vp]
@@ -263,6 +294,40 @@ _PKEYS = ("g", "Bd", "cfl", "ema_alpha", "dt_init", "dt_min", "dt_max", "frictio
           "ramp_time", "timeout_s")
 
 
+def case_args(case: dict, precision: str = "fp32", kahan: bool = True, **overrides):
+    """bsq_params and bsq_boundary of a workload dict (see ``workloads``); the
+    third value keeps the component arrays the boundary points to alive."""
+    prm = dict(case["params"])
+    prm.update(overrides)
+    p = bsq_params_default()
+    p.nx, p.ny = int(prm["nx"]), int(prm["ny"])
+    p.dx, p.dy = float(prm["dx"]), float(prm["dy"])
+    for k in _PKEYS:
+        if k in prm:
+            setattr(p, k, float(prm[k]))
+    p.precision = FP64 if precision == "fp64" else FP32
+    p.kahan = 1 if kahan else 0
+    p.cross_mode = int(prm.get("cross_mode", 1))
+    if "graph_steps" in prm:
+        p.graph_steps = int(prm["graph_steps"])
+    for q, v in enumerate(prm.get("tune", ()) or ()):
+        p.tune[q] = int(v)
+    b = bsq_boundary()
+    bc = prm.get("bc", (WALL, WALL, WALL, WALL))
+    sw = prm.get("sponge_width", (0.0, 0.0, 0.0, 0.0))
+    for s in range(4):
+        b.type[s] = int(bc[s])
+        b.sponge_width[s] = float(sw[s])
+    comps = case.get("comps")
+    keep = None
+    if comps is not None and len(comps):
+        c = np.ascontiguousarray(np.asarray(comps, dtype=np.float64).T)
+        keep = c
+        b.n_comp = c.shape[1]
+        b.amp, b.freq, b.phase, b.dir = (_ptr(c[k]) for k in range(4))
+    return p, b, keep
+
+
 class Domain:
     """A domain on the GPU built from a workload dict (see ``workloads``):
     ``params`` (nx, ny, dx, dy, bc, sponge_width, ...), ``bed`` corners,
@@ -271,34 +336,7 @@ class Domain:
 
     def __init__(self, case: dict, precision: str = "fp32", kahan: bool = True, stream: int | None = None,
                  **overrides):
-        prm = dict(case["params"])
-        prm.update(overrides)
-        p = bsq_params_default()
-        p.nx, p.ny = int(prm["nx"]), int(prm["ny"])
-        p.dx, p.dy = float(prm["dx"]), float(prm["dy"])
-        for k in _PKEYS:
-            if k in prm:
-                setattr(p, k, float(prm[k]))
-        p.precision = FP64 if precision == "fp64" else FP32
-        p.kahan = 1 if kahan else 0
-        p.cross_mode = int(prm.get("cross_mode", 1))
-        if "graph_steps" in prm:
-            p.graph_steps = int(prm["graph_steps"])
-        for q, v in enumerate(prm.get("tune", ()) or ()):
-            p.tune[q] = int(v)
-        b = bsq_boundary()
-        bc = prm.get("bc", (WALL, WALL, WALL, WALL))
-        sw = prm.get("sponge_width", (0.0, 0.0, 0.0, 0.0))
-        for s in range(4):
-            b.type[s] = int(bc[s])
-            b.sponge_width[s] = float(sw[s])
-        comps = case.get("comps")
-        self._comps = None
-        if comps is not None and len(comps):
-            c = np.ascontiguousarray(np.asarray(comps, dtype=np.float64).T)
-            self._comps = c
-            b.n_comp = c.shape[1]
-            b.amp, b.freq, b.phase, b.dir = (_ptr(c[k]) for k in range(4))
+        p, b, self._comps = case_args(case, precision, kahan, **overrides)
         self.nx, self.ny = p.nx, p.ny
         self.precision = precision
         self.params = p
@@ -372,6 +410,99 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             bsq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def bsq_clock(h) -> tuple:
+    t, n = ctypes.c_double(), ctypes.c_longlong()
+    st = lib().bsq_clock(h, ctypes.byref(t), ctypes.byref(n))
+    return t.value, n.value, st
+
+
+def bsq_domain_bytes(params: bsq_params, n_comp: int = 0) -> int:
+    return lib().bsq_domain_bytes(ctypes.byref(params), int(n_comp))
+
+
+class Server:
+    """Continuous batching of simulation requests (``bsq_server_*``)."""
+
+    def __init__(self, hbm_budget: int = 0, max_slots: int = 64, steps_per_round: int = 32,
+                 precision: str = "fp32", kahan: bool = True, stream: int | None = None):
+        cfg = bsq_server_config()
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.max_slots = int(max_slots)
+        cfg.steps_per_round = int(steps_per_round)
+        cfg.precision = FP64 if precision == "fp64" else FP32
+        cfg.kahan = 1 if kahan else 0
+        cfg.cuda_stream = stream or 0
+        self.precision, self.kahan = precision, kahan
+        self._shape = {}
+        h = ctypes.c_void_p()
+        st = lib().bsq_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise BsqError(st, "bsq_server_create")
+        self.h = h
+
+    def submit(self, case: dict, t_end: float) -> int:
+        p, b, keep = case_args(case, self.precision, self.kahan)
+        arrs = [_f64(case.get(k)) for k in ("bed", "eta0", "P0", "Q0")]
+        rid = ctypes.c_longlong()
+        st = lib().bsq_server_submit(self.h, ctypes.byref(p), _ptr(arrs[0]), ctypes.byref(b), _ptr(arrs[1]),
+                                     _ptr(arrs[2]), _ptr(arrs[3]), float(t_end), ctypes.byref(rid))
+        del keep
+        if st != OK:
+            raise BsqError(st, "bsq_server_submit")
+        self._shape[rid.value] = (p.nx, p.ny)
+        return rid.value
+
+    def poll(self) -> tuple:
+        nr, npd = ctypes.c_int(), ctypes.c_int()
+        st = lib().bsq_server_poll(self.h, ctypes.byref(nr), ctypes.byref(npd))
+        if st != OK:
+            raise BsqError(st, "bsq_server_poll")
+        return nr.value, npd.value
+
+    def request(self, rid: int) -> dict:
+        state, stat = ctypes.c_int(), ctypes.c_int()
+        t, n = ctypes.c_double(), ctypes.c_longlong()
+        st = lib().bsq_server_request(self.h, int(rid), ctypes.byref(state), ctypes.byref(t), ctypes.byref(n),
+                                      ctypes.byref(stat))
+        if st != OK:
+            raise BsqError(st, "bsq_server_request")
+        return dict(state=state.value, t=t.value, steps=n.value, status=stat.value)
+
+    def read(self, rid: int, field: str) -> np.ndarray:
+        nx, ny = self._shape[rid]
+        out = np.empty((ny, nx), dtype=np.float64)
+        st = lib().bsq_server_read(self.h, int(rid), FIELDS[field], _ptr(out))
+        if st != OK:
+            raise BsqError(st, "bsq_server_read")
+        return out
+
+    def release(self, rid: int) -> None:
+        st = lib().bsq_server_release(self.h, int(rid))
+        if st != OK:
+            raise BsqError(st, "bsq_server_release")
+        self._shape.pop(rid, None)
+
+    def bytes_in_use(self) -> int:
+        return lib().bsq_server_bytes_in_use(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bsq_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

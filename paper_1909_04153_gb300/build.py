@@ -1,6 +1,6 @@
 """Build the CUDA library in-tree: ``_build/libbsq.so`` for sm_103a.
 
-Two translation units are compiled in parallel with nvcc and linked into one
+The translation units are compiled in parallel with nvcc and linked into one
 shared library with the C ABI of ``include/bsq.h``.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libbsq.so")
-SOURCES = ["bsq_kernels.cu", "bsq_host.cu", "bsq_noalloc.cu"]
+SOURCES = ["bsq_kernels.cu", "bsq_host.cu", "bsq_noalloc.cu", "bsq_server.cu"]
 HEADERS = ["bsq_internal.cuh", "bsq_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The step kernels compile single-precision sqrt, division and reciprocal to

@@ -138,6 +138,48 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------------ create
 
+// Byte offsets of everything in a domain's one device allocation.
+struct Layout {
+    size_t fb;  // bytes per padded field
+    int nfields;
+    size_t o_fields, o_corner, o_gx, o_gy, o_corr, o_cb, o_comp, o_ctl, o_coef, o_mass, o_ysum, total;
+};
+constexpr int kMassBlocks = 512;
+
+template <typename T>
+static Layout layout(int nx, int ny, int tune_xk, bool kahan, int nc)
+{
+    Layout L;
+    const int pitch = row_pitch<T>(nx, tune_xk);
+    const long long fs = (long long)pitch * (ny + 4);
+    L.fb = align256((size_t)fs * sizeof(T));
+    const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
+    L.nfields = nstate + 15 + 2 + 1 + 6;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    L.o_fields = take(L.fb * L.nfields);
+    L.o_corner = take((size_t)(nx + 5) * (ny + 5) * sizeof(T));
+    L.o_gx = take((size_t)pitch * sizeof(T));  // row-length vector loads
+    L.o_gy = take(ny * sizeof(T));
+    L.o_corr = take((size_t)(4 * nx + 4 * ny + 4) * sizeof(T));
+    L.o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
+    L.o_comp = take((size_t)7 * (nc > 0 ? nc : 1) * sizeof(double));
+    L.o_ctl = take(sizeof(Ctl));
+    L.o_coef = take(sizeof(Coef));
+    L.o_mass = take(kMassBlocks * sizeof(double));
+    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;  // room for the smallest chunks
+    L.o_ysum = take(7 * nchy * sizeof(T));
+    L.total = off;
+    return L;
+}
+
+extern "C" size_t bsq_domain_bytes(const bsq_params *p, int n_comp)
+{
+    if (!p || p->nx < 3 || p->ny < 3 || p->nx > 16384 || p->ny > 16384) return 0;
+    if (p->precision == BSQ_FP64) return layout<double>(p->nx, p->ny, p->tune[4], false, n_comp).total;
+    return layout<float>(p->nx, p->ny, p->tune[4], p->kahan != 0, n_comp).total;
+}
+
 template <typename T>
 static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0, const double *P0,
                            const double *Q0)
@@ -296,22 +338,15 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     for (size_t q = 0; q < (size_t)fs; q++) bCT[q] = (T)bC[q];
 
     // ---- device memory: one allocation
-    const size_t fb = align256((size_t)fs * sizeof(T));
+    const Layout L = layout<T>(nx, ny, p.tune[4], kahan, nc);
+    const size_t fb = L.fb;
+    const int nfields = L.nfields;
+    const size_t o_fields = L.o_fields, o_corner = L.o_corner, o_gx = L.o_gx, o_gy = L.o_gy, o_corr = L.o_corr;
+    const size_t o_cb = L.o_cb, o_comp = L.o_comp, o_ctl = L.o_ctl, o_coef = L.o_coef, o_mass = L.o_mass;
+    const size_t o_ysum = L.o_ysum, off = L.total;
     const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
-    const int nfields = nstate + 15 + 2 + 1 + 6;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    size_t o_fields = take(fb * nfields);
-    size_t o_corner = take(cornerT.size() * sizeof(T));
-    size_t o_gx = take((size_t)pitch * sizeof(T)), o_gy = take(ny * sizeof(T));  // gx: row-length vector loads
-    size_t o_corr = take((size_t)(4 * nx + 4 * ny + 4) * sizeof(T));
-    size_t o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
-    size_t o_comp = take(comp.size() * sizeof(double));
-    size_t o_ctl = take(sizeof(Ctl)), o_coef = take(sizeof(Coef));
-    dm->mass_blocks = 512;
-    size_t o_mass = take(dm->mass_blocks * sizeof(double));
-    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;  // room for the smallest chunks
-    size_t o_ysum = take(7 * nchy * sizeof(T));
+    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;
+    dm->mass_blocks = kMassBlocks;
     dm->dbytes = off;
     if (cudaMalloc(&dm->dmem, off) != cudaSuccess) { dm->dmem = nullptr; return BSQ_ERR_OOM; }
     char *base = (char *)dm->dmem;
@@ -474,6 +509,7 @@ extern "C" bsq_status bsq_create(const bsq_params *p, const double *bed_corners,
         bsq_destroy(d);
         return BSQ_ERR_OOM;
     }
+    memset((void *)d->h_ctl, 0, sizeof(Ctl));  // t = 0, n = 0 until the first advance
     bsq_status st = d->fp64 ? create_T<double>(d, bed_corners, eta0, P0, Q0)
                             : create_T<float>(d, bed_corners, eta0, P0, Q0);
     d->bnd.amp = d->bnd.freq = d->bnd.phase = d->bnd.dir = nullptr;
@@ -941,6 +977,16 @@ extern "C" bsq_status bsq_info(const bsq_domain *d, double *t, long long *n, dou
         *mass = s * d->p.dx * d->p.dy;
     }
     return ctl_status(c) == BSQ_OK ? d->sticky : ctl_status(c);
+}
+
+extern "C" bsq_status bsq_clock(const bsq_domain *d, double *t, long long *n)
+{
+    if (!d) return BSQ_ERR_ARG;
+    const Ctl &c = *d->h_ctl;
+    if (t) *t = c.t;
+    if (n) *n = c.n;
+    if (d->sticky != BSQ_OK) return d->sticky;
+    return ctl_status(c);
 }
 
 // ------------------------------------------------------------------ checkpoint

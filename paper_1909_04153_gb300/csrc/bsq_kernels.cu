@@ -82,6 +82,23 @@ __device__ double maker_ramp(const Dev<T> &D, double t)
     return D.ramp_time > 0.0 ? tanh(3.0 * t / D.ramp_time) : 1.0;
 }
 
+// sin and cos of a phase given in FP64, to single precision, for the
+// single-precision path: the phase is reduced by quadrants in FP64,
+// r = ph - n pi/2 with |r| <= pi/4, then the Taylor series of sin (through
+// r^9) and cos (through r^10) are summed in FP32 (truncation below 2e-9 on
+// |r| <= pi/4) and rotated back by the quadrant n mod 4.
+__device__ __forceinline__ void sincos_phase_f(double ph, float &s, float &c)
+{
+    const double n = rint(ph * 0.63661977236758134);  // 2 / pi
+    const float r = (float)(ph - n * 1.5707963267948966);
+    const float r2 = r * r;
+    const float sr = r * (1.0f - r2 * (1.0f / 6.0f - r2 * (1.0f / 120.0f - r2 * (1.0f / 5040.0f - r2 * (1.0f / 362880.0f)))));
+    const float cr = 1.0f - r2 * (0.5f - r2 * (1.0f / 24.0f - r2 * (1.0f / 720.0f - r2 * (1.0f / 40320.0f - r2 * (1.0f / 3628800.0f)))));
+    const int q = (int)((long long)n & 3);
+    s = q == 0 ? sr : (q == 1 ? cr : (q == 2 ? -sr : -cr));
+    c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
+}
+
 // Linear wave-maker state (eta, P, Q) at (x, y, t) with ramp value r, in FP64.
 template <typename T>
 __device__ void maker_state(const Dev<T> &D, double x, double y, double t, double r, double &e, double &p, double &q)
@@ -91,10 +108,9 @@ __device__ void maker_state(const Dev<T> &D, double x, double y, double t, doubl
         const double ph = D.kx[k] * x + D.ky[k] * y - D.om[k] * t + D.ph[k];
         double c;
         if (sizeof(T) == 4) {
-            // single-precision path: reduce the phase to [-pi, pi] in FP64,
-            // then a single-precision cosine of the reduced angle
-            const double red = ph - 6.283185307179586 * rint(ph * 0.15915494309189535);
-            c = (double)cosf((float)red);
+            float sf, cf;
+            sincos_phase_f(ph, sf, cf);
+            c = (double)cf;
         } else {
             c = cos(ph);
         }
@@ -106,6 +122,47 @@ __device__ void maker_state(const Dev<T> &D, double x, double y, double t, doubl
     e = r * se;
     p = r * sp;
     q = r * sq;
+}
+
+// Increments of the maker fluxes from (t0, r0) to (t1, r1) at (x, y), and Q
+// at t1.  They enter the boundary rows of the line systems as -A (g^{n+1} - g^n),
+// a small difference of two maker values; in single precision it is formed
+// from the identity
+//   r1 cos(ph0 + d) - r0 cos(ph0) = cos(ph0) ((r1 - r0) + r1 (cos d - 1)) - r1 sin(ph0) sin d,
+// d = -omega (t1 - t0), with sin d and cos d - 1 from their Taylor series, so
+// the increment keeps single-precision relative accuracy instead of the
+// absolute error of two cosines.
+template <typename T>
+__device__ void maker_increment(const Dev<T> &D, double x, double y, double t0, double t1, double r0, double r1,
+                                double &dp, double &dq, double &q1)
+{
+    if (sizeof(T) == 8) {
+        double e0, p0, q0, e1, p1;
+        maker_state(D, x, y, t0, r0, e0, p0, q0);
+        maker_state(D, x, y, t1, r1, e1, p1, q1);
+        dp = p1 - p0;
+        dq = q1 - q0;
+        return;
+    }
+    float sp = 0.0f, sq = 0.0f, sq1 = 0.0f;
+    const float dr = (float)(r1 - r0), r1f = (float)r1;
+    for (int k = 0; k < D.ncomp; k++) {
+        const double ph0 = D.kx[k] * x + D.ky[k] * y - D.om[k] * t0 + D.ph[k];
+        float s0, c0;
+        sincos_phase_f(ph0, s0, c0);
+        const float d = (float)(-D.om[k] * (t1 - t0)), d2 = d * d;
+        const float sd = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
+        const float cm1 = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+        const float term = c0 * (dr + r1f * cm1) - r1f * s0 * sd;
+        const float c1 = c0 + (c0 * cm1 - s0 * sd);
+        const float a = (float)D.amp[k];
+        sp += (float)D.cx[k] * a * term;
+        sq += (float)D.cy[k] * a * term;
+        sq1 += (float)D.cy[k] * a * c1;
+    }
+    dp = (double)sp;
+    dq = (double)sq;
+    q1 = (double)(r1f * sq1);
 }
 
 // ------------------------------------------------------------------ controller
@@ -308,11 +365,10 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                 if (D.bc[s] == MAKER) {
                     double x = side == 0 ? -0.5 * D.dxd : ((double)nx + 0.5) * D.dxd;
                     double y = ((double)j + 0.5) * D.dyd;
-                    double e0, p0, q0, e1, p1, q1;
-                    maker_state(D, x, y, t0, r0, e0, p0, q0);
-                    maker_state(D, x, y, t1, r1, e1, p1, q1);
+                    double dp, dq, q1;
+                    maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
                     double a = side == 0 ? D.cW[j] : D.cE[j];
-                    corr = (T)(-a * (p1 - p0));
+                    corr = (T)(-a * dp);
                     (side == 0 ? D.mqW : D.mqE)[j] = (T)q1;
                 }
                 (side == 0 ? D.corrW : D.corrE)[j] = corr;
@@ -324,11 +380,10 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                 if (D.bc[s] == MAKER) {
                     double x = ((double)i + 0.5) * D.dxd;
                     double y = side == 0 ? -0.5 * D.dyd : ((double)ny + 0.5) * D.dyd;
-                    double e0, p0, q0, e1, p1, q1;
-                    maker_state(D, x, y, t0, r0, e0, p0, q0);
-                    maker_state(D, x, y, t1, r1, e1, p1, q1);
+                    double dp, dq, q1, e1, p1;
+                    maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
                     double a = side == 0 ? D.cS[i] : D.cN[i];
-                    corr = (T)(-a * (q1 - q0));
+                    corr = (T)(-a * dq);
                     (side == 0 ? D.mqS : D.mqN)[i + 1] = (T)q1;
                     if (i == 0 || i == nx - 1) {
                         // the corner columns -1 and nx of the ghost row
@@ -1337,6 +1392,29 @@ __device__ __forceinline__ void load_halo_chunk(const T *row, int ib, int lane, 
     T right = __shfl_down_sync(0xffffffffu, v[1], 1);
     if (lane == 0) left = row[ib - 1];
     if (lane == 31) right = row[ib + K];
+    v[0] = left;
+    v[K + 1] = right;
+}
+
+// vload_k when pred, zeros otherwise (no memory access)
+template <typename T, int K>
+__device__ __forceinline__ void vload_k_if(bool pred, const T *p, T *out)
+{
+    if (pred) {
+        vload_k<T, K>(p, out);
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; q++) out[q] = (T)0;
+    }
+}
+template <typename T, int K>
+__device__ __forceinline__ void load_halo_chunk_if(bool pred, const T *row, int ib, int lane, T *v)
+{
+    vload_k_if<T, K>(pred, row + ib, v + 1);
+    T left = __shfl_up_sync(0xffffffffu, v[K], 1);
+    T right = __shfl_down_sync(0xffffffffu, v[1], 1);
+    if (lane == 0) left = row[ib - 1];
+    if (lane == 31 && pred) right = row[ib + K];
     v[0] = left;
     v[K + 1] = right;
 }
@@ -2414,18 +2492,21 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
     int c0 = 0;
     for (; c0 < nx; c0 += 32 * K) {
         const int ib = c0 + lane * K;
+        // lanes past the row end load nothing; the lane holding column nx still
+        // loads (its first element is the right neighbour of the last cell)
+        const bool act = ib <= nx;
         T r[K], m[K], e[K];
-        vload_k<T, K>(D.dU + rowo + ib, r);
-        vload_k<T, K>(D.fxm + rowo + ib, m);
-        vload_k<T, K>(D.fxe + rowo + ib, e);
+        vload_k_if<T, K>(act, D.dU + rowo + ib, r);
+        vload_k_if<T, K>(act, D.fxm + rowo + ib, m);
+        vload_k_if<T, K>(act, D.fxe + rowo + ib, e);
         if (seq) {
             T Qc[K + 2], bc_[K + 2], qm[K + 2], qp[K + 2], bm[K], bp[K];
-            load_halo_chunk<T, K>(Qr, ib, lane, Qc);
-            load_halo_chunk<T, K>(br, ib, lane, bc_);
-            load_halo_chunk<T, K>(Qr - D.pitch, ib, lane, qm);
-            load_halo_chunk<T, K>(Qr + D.pitch, ib, lane, qp);
-            vload_k<T, K>(br - D.pitch + ib, bm);
-            vload_k<T, K>(br + D.pitch + ib, bp);
+            load_halo_chunk_if<T, K>(act, Qr, ib, lane, Qc);
+            load_halo_chunk_if<T, K>(act, br, ib, lane, bc_);
+            load_halo_chunk_if<T, K>(act, Qr - D.pitch, ib, lane, qm);
+            load_halo_chunk_if<T, K>(act, Qr + D.pitch, ib, lane, qp);
+            vload_k_if<T, K>(act, br - D.pitch + ib, bm);
+            vload_k_if<T, K>(act, br + D.pitch + ib, bp);
             // ghosts of Q^{n+1} at t_{n+1}, as in k_xsolve_pipe
             if (ib == 0) {
                 if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
@@ -2496,15 +2577,16 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
     T *wrow = D.w[cf.wc ^ 1] + rowo;
     for (c0 -= 32 * K; c0 >= 0; c0 -= 32 * K) {
         const int ib = c0 + lane * K;
+        const bool act = ib < nx;
         T x[K], c[K], Pv[K], cPv[K], wv[K], Qv[K], bv[K], gxv[K];
         vload_k<T, K>(ys + ib, x);
-        vload_k<T, K>(D.gx + ib, gxv);
-        vload_k<T, K>(D.fxc + rowo + ib, c);
-        vload_k<T, K>(Pr + ib, Pv);
-        if (D.kahan) vload_k<T, K>(cPr + ib, cPv);
-        vload_k<T, K>(wrow + ib, wv);
-        vload_k<T, K>(Qr + ib, Qv);
-        vload_k<T, K>(br + ib, bv);
+        vload_k_if<T, K>(act, D.gx + ib, gxv);
+        vload_k_if<T, K>(act, D.fxc + rowo + ib, c);
+        vload_k_if<T, K>(act, Pr + ib, Pv);
+        vload_k_if<T, K>(act && D.kahan, cPr + ib, cPv);
+        vload_k_if<T, K>(act, wrow + ib, wv);
+        vload_k_if<T, K>(act, Qr + ib, Qv);
+        vload_k_if<T, K>(act, br + ib, bv);
 #pragma unroll
         for (int q = 0; q < K; q++)
             if (ib + q >= nx) { c[q] = (T)0; x[q] = (T)0; }
@@ -2607,7 +2689,7 @@ __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsig
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(32 * XW_WARPS) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
+__global__ void __launch_bounds__(32 * XW_WARPS, sizeof(T) == 4 ? 4 : 2) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
 {
     xsolve_warp_body<T, K>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
 }
@@ -3053,7 +3135,7 @@ __global__ void __launch_bounds__(256) k_yapply_b(const Dev<T> *Ds, const int4 *
 // table entry: (domain, block of that domain, that domain's block count,
 // shared row length of the domain)
 template <typename T, int K>
-__global__ void __launch_bounds__(32 * XW_WARPS) k_xsolve_warp_b(const Dev<T> *Ds, const int4 *tab)
+__global__ void __launch_bounds__(32 * XW_WARPS, sizeof(T) == 4 ? 4 : 2) k_xsolve_warp_b(const Dev<T> *Ds, const int4 *tab)
 {
     const int4 e = tab[blockIdx.x];
     const Dev<T> &D = batch_dev(Ds, e.x);
