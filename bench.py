@@ -367,6 +367,7 @@ def run_batched(args, dev, stream):
     doms = [bsq.Domain(c, precision="fp32", stream=stream.cuda_stream, graph_steps=args.graph_steps)
             for c in cases]
     batch = bsq.Batch(doms, stream=stream.cuda_stream)
+    tuned = batch.autotune(args.batch_tune_steps) if args.batch_tune_steps > 0 else None
     batch.advance(max_steps=10)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -407,7 +408,7 @@ def run_batched(args, dev, stream):
                     "solitary or JONSWAP maker (seeded 50/50)" % len(cases),
         "domains": len(cases), "cells": int(total), "precision": "fp32", "kahan": True,
         "value": value, "unit": "cell-updates/s", "ms_per_step": ms / args.batch_steps,
-        "steps": args.batch_steps, "launches_per_step": launches,
+        "steps": args.batch_steps, "launches_per_step": launches, "autotuned_shapes": tuned,
         "gpu_launches": launches * args.graph_steps * math.ceil(args.batch_steps / args.graph_steps) + 1,
         "one_at_a_time_fp32": {"value": v32, "unit": "cell-updates/s", "steps_each": args.batch_solo_steps},
         "one_at_a_time_fp64": {"value": v64, "unit": "cell-updates/s", "steps_each": args.batch_fp64_steps},
@@ -517,6 +518,7 @@ def main(argv=None):
     ap.add_argument("--batch-domains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-solo-steps", type=int, default=32)
+    ap.add_argument("--batch-tune-steps", type=int, default=16)
     ap.add_argument("--batch-fp64-steps", type=int, default=16)
     ap.add_argument("--tune", type=lambda s: tuple(int(v) for v in s.split(",")), default=None,
                     help="kernel shape knobs (bsq_params.tune), comma separated")

@@ -217,6 +217,14 @@ bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *cuda_stream
  * errors: BSQ_ERR_ARG, BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
 bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long long max_steps, long long *steps_done);
 
+/* Autotuner of the batch's tile shapes: times every combination of RHS rows
+ * per warp (64, 32), x-line elements per lane (8, 4; FP64: 4) and y-line rows
+ * per chunk (8, 16) over steps_per_trial steps (plus one warm-up graph) on
+ * the batch itself -- real steps: every member advances -- and keeps the
+ * fastest.  choice (NULL or 3 ints) receives {rows, x elements, y rows}.  The
+ * shapes change the rounding order of the line solves, not the method. */
+bsq_status bsq_batch_autotune(bsq_batch *b, long long steps_per_trial, int *choice);
+
 /* Members of the batch; kernel launches per batched step. */
 int bsq_batch_size(const bsq_batch *b);
 int bsq_batch_launches_per_step(const bsq_batch *b);

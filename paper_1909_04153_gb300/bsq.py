@@ -112,6 +112,8 @@ def lib():
         L.bsq_batch_launches_per_step.restype = ctypes.c_int
         L.bsq_batch_launches_per_step.argtypes = [vp]
         L.bsq_batch_destroy.argtypes = [vp]
+        L.bsq_batch_autotune.restype = ctypes.c_int
+        L.bsq_batch_autotune.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
         L.bsq_clock.restype = ctypes.c_int
         L.bsq_clock.argtypes = [vp, _DP, ctypes.POINTER(ctypes.c_longlong)]
         L.bsq_domain_bytes.restype = sz
@@ -406,6 +408,14 @@ class Batch:
 
     def launches_per_step(self) -> int:
         return lib().bsq_batch_launches_per_step(self.h)
+
+    def autotune(self, steps_per_trial: int = 16) -> dict:
+        """Pick the fastest tile shapes on this batch (advances every member)."""
+        ch = (ctypes.c_int * 3)()
+        st = lib().bsq_batch_autotune(self.h, int(steps_per_trial), ch)
+        if st != OK:
+            raise BsqError(st, "bsq_batch_autotune")
+        return dict(rhs_rows=ch[0], x_elements=ch[1], y_rows=ch[2])
 
     def close(self):
         if getattr(self, "h", None):

@@ -696,15 +696,25 @@ static void batch_free(bsq_batch *b)
     delete b;
 }
 
-// The block tables of every stage for the member domains; each domain's
-// blocks are laid out exactly as its own single-domain launches lay them out.
+// The block tables of every stage for the member domains with the given tile
+// shapes (RHS rows per warp, x elements per lane, y rows per chunk); with the
+// defaults each domain's blocks are laid out exactly as its own single-domain
+// launches lay them out.
 template <typename T>
-static bsq_status batch_build(bsq_batch *b)
+static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
 {
     const int n = (int)b->doms.size();
     std::vector<int4> tg, tr, ts, tc, tx;
     bool fast = true, theta1 = true;
-    const int K = batch_xchunk<T>();
+    if (b->dmem) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->dmem);
+        b->dmem = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     int yrow_max = 32 * K;
     std::vector<Dev<T>> hD(n);
     for (int d = 0; d < n; d++) {
@@ -718,10 +728,10 @@ static bsq_status batch_build(bsq_batch *b)
         const long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
         const int gb = (int)((nwork + 255) / 256);
         for (int q = 0; q < gb; q++) tg.push_back(make_int4(d, q, gb, 0));
-        const int nstrip = (nx + 27) / 28, nband = (ny + 63) / 64;
+        const int nstrip = (nx + 27) / 28, nband = (ny + rows - 1) / rows;
         const int rb = (int)(((long long)nstrip * nband + 3) / 4);
         for (int q = 0; q < rb; q++) tr.push_back(make_int4(d, q, nstrip, 0));
-        const int nch = (ny + 7) / 8;
+        const int nch = (ny + KY - 1) / KY;
         const int gx = (nx + 31) / 32, gy = (nch + 7) / 8;
         for (int by = 0; by < gy; by++)
             for (int bx = 0; bx < gx; bx++) ts.push_back(make_int4(d, bx, by, nch));
@@ -761,6 +771,9 @@ static bsq_status batch_build(bsq_batch *b)
     P.rhs_fast = fast ? 1 : 0;
     P.rhs_theta1 = theta1 ? 1 : 0;
     P.yrow_max = yrow_max;
+    P.rhs_rows = rows;
+    P.xk = K;
+    P.ky = KY;
     CK(configure_batch<T>(yrow_max));
     return BSQ_OK;
 }
@@ -805,7 +818,8 @@ extern "C" bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *
         batch_free(b);
         return BSQ_ERR_OOM;
     }
-    bsq_status st = b->fp64 ? batch_build<double>(b) : batch_build<float>(b);
+    bsq_status st = b->fp64 ? batch_build<double>(b, 64, batch_xchunk<double>(), 8)
+                            : batch_build<float>(b, 64, batch_xchunk<float>(), 8);
     if (st != BSQ_OK) {
         batch_free(b);
         return st;
@@ -908,6 +922,48 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
 extern "C" int bsq_batch_size(const bsq_batch *b) { return b ? (int)b->doms.size() : 0; }
 
 extern "C" int bsq_batch_launches_per_step(const bsq_batch *b) { return b ? 6 : 0; }
+
+// Try every tile-shape combination on the batch itself (real steps), keep the
+// fastest.
+extern "C" bsq_status bsq_batch_autotune(bsq_batch *b, long long steps_per_trial, int *choice)
+{
+    if (!b || steps_per_trial < 1) return BSQ_ERR_ARG;
+    const int n = (int)b->doms.size();
+    const int ks_f[2] = {8, 4}, ks_d[1] = {4};
+    const int *ks = b->fp64 ? ks_d : ks_f;
+    const int nk = b->fp64 ? 1 : 2;
+    const int rows_c[2] = {64, 32}, ky_c[2] = {8, 16};
+    double best = 1e300;
+    int br = 64, bk = ks[0], bky = 8;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<long long> done(n);
+    bsq_status st = BSQ_OK;
+    for (int ir = 0; ir < 2 && st == BSQ_OK; ir++)
+        for (int ik = 0; ik < nk && st == BSQ_OK; ik++)
+            for (int iy = 0; iy < 2 && st == BSQ_OK; iy++) {
+                st = b->fp64 ? batch_build<double>(b, rows_c[ir], ks[ik], ky_c[iy])
+                             : batch_build<float>(b, rows_c[ir], ks[ik], ky_c[iy]);
+                if (st != BSQ_OK) break;
+                st = bsq_batch_advance(b, nullptr, b->graph_steps, done.data());  // warm-up, builds the graph
+                if (st != BSQ_OK) break;
+                cudaEventRecord(e0, b->stream);
+                st = bsq_batch_advance(b, nullptr, steps_per_trial, done.data());
+                cudaEventRecord(e1, b->stream);
+                if (st != BSQ_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { st = BSQ_ERR_CUDA; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; br = rows_c[ir]; bk = ks[ik]; bky = ky_c[iy]; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != BSQ_OK) return st;
+    st = b->fp64 ? batch_build<double>(b, br, bk, bky) : batch_build<float>(b, br, bk, bky);
+    if (st == BSQ_OK && choice) { choice[0] = br; choice[1] = bk; choice[2] = bky; }
+    return st;
+}
 
 // ------------------------------------------------------------------ outputs
 

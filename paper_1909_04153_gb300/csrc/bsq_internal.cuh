@@ -96,6 +96,8 @@ struct BatchPlan {
     const int4 *t_ghost, *t_rhs, *t_ysum, *t_yscan, *t_x;
     int rhs_fast, rhs_theta1;                     // RHS variant shared by all domains
     int yrow_max;                                 // x-solver shared row length (elements)
+    int rhs_rows, xk, ky;                         // tile shapes: RHS rows per warp, x elements per
+                                                  // lane, y rows per chunk (the autotuner's knobs)
 };
 
 template <typename T>

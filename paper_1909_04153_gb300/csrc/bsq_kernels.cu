@@ -3179,23 +3179,33 @@ template <typename T>
 cudaError_t configure_batch(int yrow_max)
 {
     const int bytes = XW_WARPS * yrow_max * (int)sizeof(T);
-    if (batch_xchunk<T>() == 8)
-        return cudaFuncSetAttribute(k_xsolve_warp_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return cudaFuncSetAttribute(k_xsolve_warp_b<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_xsolve_warp_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_warp_b<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+template <typename T, int ROWS>
+static void launch_batch_rhs(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
+{
+    if (P.rhs_fast) k_rhs_sw_b<T, ROWS, true, true><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    else if (P.rhs_theta1) k_rhs_sw_b<T, ROWS, true, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    else k_rhs_sw_b<T, ROWS, false, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
 }
 
 template <typename T>
 cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
 {
     k_ghost_b<T><<<P.nb_ghost, 256, 0, st>>>(Ds, P.t_ghost);
-    if (P.rhs_fast) k_rhs_sw_b<T, 64, true, true><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
-    else if (P.rhs_theta1) k_rhs_sw_b<T, 64, true, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
-    else k_rhs_sw_b<T, 64, false, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
-    k_ysum_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    if (P.rhs_rows == 32) launch_batch_rhs<T, 32>(Ds, P, st);
+    else launch_batch_rhs<T, 64>(Ds, P, st);
+    if (P.ky == 16) k_ysum_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    else k_ysum_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
     k_yscan_b<T><<<P.nb_yscan, 256, 0, st>>>(Ds, P.t_yscan);
-    k_yapply_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    if (P.ky == 16) k_yapply_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    else k_yapply_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
     const size_t xs = (size_t)XW_WARPS * P.yrow_max * sizeof(T);
-    if (batch_xchunk<T>() == 8) k_xsolve_warp_b<T, 8><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
+    if (P.xk == 8) k_xsolve_warp_b<T, 8><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
     else k_xsolve_warp_b<T, 4><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
     return cudaGetLastError();
 }

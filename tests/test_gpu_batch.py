@@ -150,3 +150,31 @@ def test_batch_rejects_mixed_precision_and_repeats():
         bsq.Batch([a, a])
     a.close()
     z.close()
+
+
+def test_autotuned_batch_keeps_fp64_parity():
+    cases = _members()[:4]
+    doms = [bsq.Domain(c, precision="fp64", graph_steps=4) for c in cases]
+    with bsq.Batch(doms) as b:
+        ch = b.autotune(steps_per_trial=4)
+        assert ch["rhs_rows"] in (32, 64) and ch["x_elements"] == 4 and ch["y_rows"] in (8, 16)
+        b.advance(max_steps=20)
+    for c, d in zip(cases, doms):
+        n = d.info()["n"]
+        with bsq.Domain(c, precision="fp64") as u:
+            u.advance(max_steps=n)
+            for k in ("eta", "P", "Q"):
+                ref = u.read(k)
+                if np.linalg.norm(ref) > 0:
+                    assert rel(d.read(k), ref) <= 1e-10, k
+        d.close()
+
+
+def test_autotune_fp32_picks_a_shape():
+    doms = [bsq.Domain(c, precision="fp32", graph_steps=4) for c in _members()[:3]]
+    with bsq.Batch(doms) as b:
+        ch = b.autotune(steps_per_trial=4)
+        assert ch["x_elements"] in (4, 8)
+        assert list(b.advance(max_steps=8)) == [8, 8, 8]
+    for d in doms:
+        d.close()
