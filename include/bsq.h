@@ -94,7 +94,8 @@ typedef struct {
                               with one row in flight; [3] rows per warp
                               of the sliding window (16, 32, 64); [4] x-solver elements per
                               thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
-                              y-solver (8, 16); [6], [7] reserved */
+                              y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
+                              of their own instead of inside the RHS kernel; [7] reserved */
 } bsq_params;
 
 typedef struct {

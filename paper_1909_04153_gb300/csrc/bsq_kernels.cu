@@ -767,7 +767,7 @@ constexpr int SW_COLS = 28;  // interior columns per warp strip (lanes 2..29)
 // form, compensated accumulation in single precision, no friction -- with
 // both history levels always read (they hold zeros, weighted by zero, during
 // the Euler start) and 32-bit offsets into the fields.
-template <typename T, int ROWS, bool THETA1, bool FAST>
+template <typename T, int ROWS, bool THETA1, bool FAST, int YS = 0>
 __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip)
 {
     const Coef cf = *D.coef;
@@ -823,6 +823,13 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
         pKR = corner[(long long)(kr + 2) * cp + (kc1 + 2)];
     };
     T hE1 = 0, hF1 = 0, hG1 = 0, hGs1 = 0, hFs1 = 0, hE2 = 0, hF2 = 0, hG2 = 0, hGs2 = 0, hFs2 = 0, hcw = 0;
+    // YS > 0: the y-line chunk summaries of the three-launch y-solver (chunks of
+    // YS rows) are formed here from the fresh dV, with the factors prefetched
+    // with the history (what k_ysum computes from dV read back)
+    T hym = 0, hye = 0, hyc = 0;
+    T yt = 0, yPi = 1, yal0 = 0, yal1 = 0, ybe = 1;
+    const int ynch = YS > 0 ? (ny + YS - 1) / YS : 0;
+    const long long ys_s = (long long)nx * ynch;
     // 32-bit offsets of the history slots (FAST: the fields fit in 2^31 elements)
     const int ifs = (int)fs, s1o = cf.s1 * (int)fs, s2o = cf.s2 * (int)fs;
     auto load_hist = [&](int o) {
@@ -830,6 +837,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
             if (FAST) {
                 const int c = (o + 2) * D.pitch + i + D.hx;
                 if (kahan) hcw = D.cw[c];
+                if (YS > 0) { hym = D.fym[c]; hye = D.fye[c]; hyc = D.fyc[c]; }
                 const T *h1 = H + (s1o + c), *h2 = H + (s2o + c);
                 hE1 = h1[0]; hF1 = h1[3 * ifs]; hG1 = h1[6 * ifs]; hGs1 = h1[12 * ifs];
                 hE2 = h2[0]; hF2 = h2[3 * ifs]; hG2 = h2[6 * ifs]; hGs2 = h2[12 * ifs];
@@ -855,6 +863,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
         T wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR;
         T cE1 = hE1, cF1 = hF1, cG1 = hG1, cGs1 = hGs1, cFs1 = hFs1;
         T cE2 = hE2, cF2 = hF2, cG2 = hG2, cGs2 = hGs2, cFs2 = hFs2, ccw = hcw;
+        const T cym = hym, cye = hye, cyc = hyc;
         if (r + 1 < rend) load_lead(r + 1);
         load_hist(r - 1);  // output row of the next step
 #pragma unroll
@@ -984,6 +993,27 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                         if (kahan) D.cw[ci] = cwn;
                         D.dU[ci] = dU;
                         D.dV[ci] = dV;
+                        if (YS > 0) {
+                            // same recurrences as k_ysum, row by row
+                            T rr = dV;
+                            if (o == 0) rr += D.corrS[i];
+                            if (o == ny - 1) rr += D.corrN[i];
+                            yt = cym * rr + cye * yt;
+                            yPi = cye * yPi;
+                            yal0 = yal0 + ybe * yt;
+                            yal1 = yal1 + ybe * yPi;
+                            ybe = -cyc * ybe;
+                            if ((o + 1) % YS == 0 || o == ny - 1) {
+                                const long long so = (long long)i * ynch + o / YS;
+                                T *sums = D.ysums;
+                                sums[so] = yPi;
+                                sums[ys_s + so] = yt;
+                                sums[2 * ys_s + so] = yal0;
+                                sums[3 * ys_s + so] = yal1;
+                                sums[4 * ys_s + so] = ybe;
+                                yt = 0; yPi = 1; yal0 = 0; yal1 = 0; ybe = 1;
+                            }
+                        }
                     }
                 } else if (valid) {
                 {
@@ -1029,10 +1059,10 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     }
 }
 
-template <typename T, int ROWS, bool THETA1, bool FAST>
+template <typename T, int ROWS, bool THETA1, bool FAST, int YS = 0>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D, int nstrip)
 {
-    rhs_sw_body<T, ROWS, THETA1, FAST>(D, blockIdx.x, nstrip);
+    rhs_sw_body<T, ROWS, THETA1, FAST, YS>(D, blockIdx.x, nstrip);
 }
 
 // ------------------------------------------------------------------ y-line solves
@@ -2910,6 +2940,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     const int nx = D.nx, ny = D.ny;
     long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
     int gb = (int)((nwork + 255) / 256);
+    bool ysum_fused = false;  // the RHS kernel forms the y-line chunk summaries
     if (ev) cudaEventRecord(ev[0], st);
     k_ghost<T><<<gb, 256, 0, st>>>(D);
     if (ev) cudaEventRecord(ev[1], st);
@@ -2925,8 +2956,18 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const int blocks = (int)((nwarp + 3) / 4);
         const bool fast = D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 &&
                           (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
+        ysum_fused = fast && D.ysplit && rows != 16 && D.tune_ysum == 0;
         const bool t1 = D.theta == (T)1;
-        if (fast) {
+        if (fast && ysum_fused) {
+            const int KY = ysplit_rows<T>(D.tune_yk);
+            if (rows == 32) {
+                if (KY == 16) k_rhs_sw<T, 32, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+                else k_rhs_sw<T, 32, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
+            } else {
+                if (KY == 16) k_rhs_sw<T, 64, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+                else k_rhs_sw<T, 64, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
+            }
+        } else if (fast) {
             if (rows == 16) k_rhs_sw<T, 16, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
             else if (rows == 32) k_rhs_sw<T, 32, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
             else k_rhs_sw<T, 64, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
@@ -2946,8 +2987,10 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const int KY = ysplit_rows<T>(D.tune_yk);
         const int nch = (ny + KY - 1) / KY;
         dim3 gb2((nx + 31) / 32, (nch + 7) / 8);
-        if (KY == 8) k_ysum<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
-        else k_ysum<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+        if (!ysum_fused) {
+            if (KY == 8) k_ysum<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+            else k_ysum<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
+        }
         k_yscan<T><<<(int)(((long long)nx * 32 + 255) / 256), 256, 0, st>>>(D, nch, D.ysums, D.yin, D.yxa);
         if (KY == 8) k_yapply<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
         else k_yapply<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
@@ -3098,12 +3141,12 @@ __global__ void __launch_bounds__(256) k_ghost_b(const Dev<T> *Ds, const int4 *t
 }
 
 // table entry: (domain, block of that domain, strips of 28 columns, 0)
-template <typename T, int ROWS, bool THETA1, bool FAST>
+template <typename T, int ROWS, bool THETA1, bool FAST, int YS = 0>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw_b(const Dev<T> *Ds, const int4 *tab)
 {
     const int4 e = tab[blockIdx.x];
     const Dev<T> &D = batch_dev(Ds, e.x);
-    rhs_sw_body<T, ROWS, THETA1, FAST>(D, e.y, e.z);
+    rhs_sw_body<T, ROWS, THETA1, FAST, YS>(D, e.y, e.z);
 }
 
 // table entry: (domain, column group, chunk group, chunks per column)
@@ -3188,7 +3231,8 @@ cudaError_t configure_batch(int yrow_max)
 template <typename T, int ROWS>
 static void launch_batch_rhs(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
 {
-    if (P.rhs_fast) k_rhs_sw_b<T, ROWS, true, true><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    if (P.rhs_fast && P.ky == 16) k_rhs_sw_b<T, ROWS, true, true, 16><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
+    else if (P.rhs_fast) k_rhs_sw_b<T, ROWS, true, true, 8><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
     else if (P.rhs_theta1) k_rhs_sw_b<T, ROWS, true, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
     else k_rhs_sw_b<T, ROWS, false, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
 }
@@ -3199,8 +3243,10 @@ cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t
     k_ghost_b<T><<<P.nb_ghost, 256, 0, st>>>(Ds, P.t_ghost);
     if (P.rhs_rows == 32) launch_batch_rhs<T, 32>(Ds, P, st);
     else launch_batch_rhs<T, 64>(Ds, P, st);
-    if (P.ky == 16) k_ysum_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
-    else k_ysum_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    if (!P.rhs_fast) {  // (the fast RHS forms the chunk summaries itself)
+        if (P.ky == 16) k_ysum_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+        else k_ysum_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
+    }
     k_yscan_b<T><<<P.nb_yscan, 256, 0, st>>>(Ds, P.t_yscan);
     if (P.ky == 16) k_yapply_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
     else k_yapply_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
