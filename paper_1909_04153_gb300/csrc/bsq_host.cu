@@ -167,7 +167,8 @@ static Layout layout(int nx, int ny, int tune_xk, bool kahan, int nc)
     L.o_ctl = take(sizeof(Ctl));
     L.o_coef = take(sizeof(Coef));
     L.o_mass = take(kMassBlocks * sizeof(double));
-    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;  // room for the smallest chunks
+    // room for the smallest chunks, each column's count rounded up to 8
+    const size_t nchy = (size_t)((ysplit_chunks<T>(ny, 8) + 7) & ~7) * nx;
     L.o_ysum = take(7 * nchy * sizeof(T));
     L.total = off;
     return L;
@@ -345,7 +346,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     const size_t o_cb = L.o_cb, o_comp = L.o_comp, o_ctl = L.o_ctl, o_coef = L.o_coef, o_mass = L.o_mass;
     const size_t o_ysum = L.o_ysum, off = L.total;
     const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
-    const size_t nchy = (size_t)ysplit_chunks<T>(ny, 8) * nx;
+    const size_t nchy = (size_t)((ysplit_chunks<T>(ny, 8) + 7) & ~7) * nx;
     dm->mass_blocks = kMassBlocks;
     dm->dbytes = off;
     if (cudaMalloc(&dm->dmem, off) != cudaSuccess) { dm->dmem = nullptr; return BSQ_ERR_OOM; }

@@ -75,6 +75,62 @@ __device__ __forceinline__ T desing_inv(T h, T eps)
 
 #define BSQ_SQRT2 1.41421356237309504880
 
+// vector loads and stores of K contiguous elements (float4 / double2)
+template <typename T> struct VecT;
+template <> struct VecT<float> { typedef float4 type; static constexpr int N = 4; };
+template <> struct VecT<double> { typedef double2 type; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vload(const T *p, T *out)
+{
+    typedef typename VecT<T>::type V;
+    V v = *reinterpret_cast<const V *>(p);
+    const T *s = reinterpret_cast<const T *>(&v);
+#pragma unroll
+    for (int q = 0; q < VecT<T>::N; q++) out[q] = s[q];
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T *p, const T *in)
+{
+    typedef typename VecT<T>::type V;
+    V v;
+    T *s = reinterpret_cast<T *>(&v);
+#pragma unroll
+    for (int q = 0; q < VecT<T>::N; q++) s[q] = in[q];
+    *reinterpret_cast<V *>(p) = v;
+}
+template <typename T, int K>
+__device__ __forceinline__ void vload_k(const T *p, T *out)
+{
+#pragma unroll
+    for (int v = 0; v < K; v += VecT<T>::N) vload(p + v, out + v);
+}
+template <typename T, int K>
+__device__ __forceinline__ void vstore_k(T *p, const T *in)
+{
+#pragma unroll
+    for (int v = 0; v < K; v += VecT<T>::N) vstore(p + v, in + v);
+}
+
+// K contiguous elements of a row starting at ib, plus one neighbour on each
+// side (v[0] and v[K+1]); neighbours come from the adjacent lanes, and from
+// memory at the ends of a warp.
+template <typename T, int K>
+__device__ __forceinline__ void load_halo_chunk(const T *row, int ib, int lane, T *v)
+{
+    vload_k<T, K>(row + ib, v + 1);
+    T left = __shfl_up_sync(0xffffffffu, v[K], 1);
+    T right = __shfl_down_sync(0xffffffffu, v[1], 1);
+    if (lane == 0) left = row[ib - 1];
+    if (lane == 31) right = row[ib + K];
+    v[0] = left;
+    v[K + 1] = right;
+}
+
+// Per-column stride of the y-line chunk summaries: the chunk count rounded up
+// to 8, so a lane's 8 chunks are one aligned vector
+__host__ __device__ __forceinline__ int ychunk_stride(int nch) { return (nch + 7) & ~7; }
+
 // Wave-maker ramp r(t) = tanh(3 t / ramp_time) (1 without a ramp).
 template <typename T>
 __device__ double maker_ramp(const Dev<T> &D, double t)
@@ -828,7 +884,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     // with the history (what k_ysum computes from dV read back)
     T hym = 0, hye = 0, hyc = 0;
     T yt = 0, yPi = 1, yal0 = 0, yal1 = 0, ybe = 1;
-    const int ynch = YS > 0 ? (ny + YS - 1) / YS : 0;
+    const int ynch = YS > 0 ? ychunk_stride((ny + YS - 1) / YS) : 0;
     const long long ys_s = (long long)nx * ynch;
     // 32-bit offsets of the history slots (FAST: the fields fit in 2^31 elements)
     const int ifs = (int)fs, s1o = cf.s1 * (int)fs, s2o = cf.s2 * (int)fs;
@@ -1209,7 +1265,8 @@ __device__ __forceinline__ void ysum_body(const Dev<T> &D, int bx, int by, int n
         al1 = al1 + be * Pi;
         be = -cc[q] * be;
     }
-    const long long s = (long long)nx * nch, o = (long long)i * nch + k;
+    const int ns = ychunk_stride(nch);
+    const long long s = (long long)nx * ns, o = (long long)i * ns + k;
     sums[o] = Pi;            // A
     sums[s + o] = yt;        // B
     sums[2 * s + o] = al0;
@@ -1232,19 +1289,25 @@ __device__ __forceinline__ void yscan_body(const Dev<T> &D, int blk, int nch, co
     const int lane = threadIdx.x & 31;
     const int nx = D.nx;
     if (i >= nx) return;
-    const long long s = (long long)nx * nch, base = (long long)i * nch;
+    const int ns = ychunk_stride(nch);
+    const long long s = (long long)nx * ns, base = (long long)i * ns;
     constexpr int CPL = 8;  // chunks per lane (nch <= 256)
-    // all five summaries of the lane's chunks are loaded up front
+    // all five summaries of the lane's chunks are loaded up front, as vectors
+    // (the per-column stride is a multiple of 8 chunks); chunks past nch are
+    // replaced by identities
     T a_[CPL], b_[CPL], s2[CPL], s3[CPL], s4[CPL];
+    const bool any = lane * CPL < nch;
+    if (any) {
+        const T *p = sums + base + lane * CPL;
+        vload_k<T, CPL>(p, a_);
+        vload_k<T, CPL>(p + s, b_);
+        vload_k<T, CPL>(p + 2 * s, s2);
+        vload_k<T, CPL>(p + 3 * s, s3);
+        vload_k<T, CPL>(p + 4 * s, s4);
+    }
 #pragma unroll
     for (int q = 0; q < CPL; q++) {
-        const int k = lane * CPL + q;
-        const bool v = k < nch;
-        a_[q] = v ? sums[base + k] : (T)1;
-        b_[q] = v ? sums[s + base + k] : (T)0;
-        s2[q] = v ? sums[2 * s + base + k] : (T)0;
-        s3[q] = v ? sums[3 * s + base + k] : (T)0;
-        s4[q] = v ? sums[4 * s + base + k] : (T)1;
+        if (lane * CPL + q >= nch) { a_[q] = (T)1; b_[q] = (T)0; s2[q] = (T)0; s3[q] = (T)0; s4[q] = (T)1; }
     }
     // forward: lane composes its chunks, warp scan, exclusive values per chunk
     T A = (T)1, B = (T)0;
@@ -1282,14 +1345,15 @@ __device__ __forceinline__ void yscan_body(const Dev<T> &D, int blk, int nch, co
     }
     T x = __shfl_down_sync(0xffffffffu, al, 1);
     if (lane == 31) x = (T)0;
+    T xk[CPL];
 #pragma unroll
     for (int q = CPL - 1; q >= 0; q--) {
-        const int k = lane * CPL + q;
-        if (k < nch) {
-            yin[base + k] = yk[q];
-            xaft[base + k] = x;
-        }
+        xk[q] = x;
         x = a_[q] + b_[q] * x;
+    }
+    if (any) {
+        vstore_k<T, CPL>(yin + base + lane * CPL, yk);
+        vstore_k<T, CPL>(xaft + base + lane * CPL, xk);
     }
 }
 
@@ -1309,7 +1373,7 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
     const int nx = D.nx, ny = D.ny;
     if (i >= nx || k >= nch) return;
     const int j0 = k * KY;
-    const long long bo = (long long)i * nch + k;
+    const long long bo = (long long)i * ychunk_stride(nch) + k;
     // all loads of a phase are issued before any store, so they overlap
     T rr[KY], mm[KY], ee[KY];
 #pragma unroll
@@ -1374,57 +1438,6 @@ __global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin,
 }
 
 // ------------------------------------------------------------------ x-line solves
-
-template <typename T> struct VecT;
-template <> struct VecT<float> { typedef float4 type; static constexpr int N = 4; };
-template <> struct VecT<double> { typedef double2 type; static constexpr int N = 2; };
-
-template <typename T>
-__device__ __forceinline__ void vload(const T *p, T *out)
-{
-    typedef typename VecT<T>::type V;
-    V v = *reinterpret_cast<const V *>(p);
-    const T *s = reinterpret_cast<const T *>(&v);
-#pragma unroll
-    for (int q = 0; q < VecT<T>::N; q++) out[q] = s[q];
-}
-template <typename T>
-__device__ __forceinline__ void vstore(T *p, const T *in)
-{
-    typedef typename VecT<T>::type V;
-    V v;
-    T *s = reinterpret_cast<T *>(&v);
-#pragma unroll
-    for (int q = 0; q < VecT<T>::N; q++) s[q] = in[q];
-    *reinterpret_cast<V *>(p) = v;
-}
-template <typename T, int K>
-__device__ __forceinline__ void vload_k(const T *p, T *out)
-{
-#pragma unroll
-    for (int v = 0; v < K; v += VecT<T>::N) vload(p + v, out + v);
-}
-template <typename T, int K>
-__device__ __forceinline__ void vstore_k(T *p, const T *in)
-{
-#pragma unroll
-    for (int v = 0; v < K; v += VecT<T>::N) vstore(p + v, in + v);
-}
-
-// K contiguous elements of a row starting at ib, plus one neighbour on each
-// side (v[0] and v[K+1]); neighbours come from the adjacent lanes, and from
-// memory at the ends of a warp.
-template <typename T, int K>
-__device__ __forceinline__ void load_halo_chunk(const T *row, int ib, int lane, T *v)
-{
-    vload_k<T, K>(row + ib, v + 1);
-    T left = __shfl_up_sync(0xffffffffu, v[K], 1);
-    T right = __shfl_down_sync(0xffffffffu, v[1], 1);
-    if (lane == 0) left = row[ib - 1];
-    if (lane == 31) right = row[ib + K];
-    v[0] = left;
-    v[K + 1] = right;
-}
 
 // vload_k when pred, zeros otherwise (no memory access)
 template <typename T, int K>
