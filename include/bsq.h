@@ -95,7 +95,9 @@ typedef struct {
                               of the sliding window (16, 32, 64); [4] x-solver elements per
                               thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
                               y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
-                              of their own instead of inside the RHS kernel; [7] reserved */
+                              of their own instead of inside the RHS kernel, bit 1: one column
+                              per lane in the single-precision RHS kernel (instead of two,
+                              paired); [7] reserved */
 } bsq_params;
 
 typedef struct {

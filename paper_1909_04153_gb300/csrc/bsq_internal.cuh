@@ -60,6 +60,7 @@ struct Dev {
     int tune_xk, tune_yk;          // x-solver elements per thread, split y-solver rows per chunk (0: default)
     int ysplit;                    // 1: three-launch y-solver (summaries, scans, apply)
     int tune_ysum;                 // 1: chunk summaries by their own kernel, not in the RHS kernel
+    int tune_rhs1;                 // 1: one column per lane in the sliding-window RHS (single precision)
     T *ysums, *yin, *yxa;          // its chunk summaries (5 per chunk) and scanned values
     int bc[4];
     // controller inputs (FP64)

@@ -1121,6 +1121,377 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_rhs_sw(Dev<T> D
     rhs_sw_body<T, ROWS, THETA1, FAST, YS>(D, blockIdx.x, nstrip);
 }
 
+// ------------------------------------------------------------------ RHS + combine, two columns per lane
+//
+// Single precision, default configuration (theta = 1, sequential cross form,
+// compensated accumulation, no friction).  Lane L of a warp holds the two
+// adjacent columns c0 = base + 2L and c0 + 1 of a strip of 60 interior columns
+// (lanes 1..30; lanes 0 and 31 are the 2-column halo on each side) and walks
+// ROWS rows like k_rhs_sw.  Both columns go through the same arithmetic, so
+// it is done on pairs with the packed single-precision instructions (two
+// results per add, multiply or fused multiply-add); comparisons, selects,
+// square roots and reciprocals stay per column.  A lane's x-neighbours come
+// from its own pair and the pairs of lanes L-1 and L+1.  Same arithmetic as
+// k_rhs_sw up to the fusion of multiply-adds.
+
+typedef float2 f2;
+__device__ __forceinline__ f2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 sc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, sc2(-1.0f), a); }  // exact a - b
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return mk2(tmax(a.x, b.x), tmax(a.y, b.y)); }
+__device__ __forceinline__ f2 min2(f2 a, f2 b) { return mk2(tmin(a.x, b.x), tmin(a.y, b.y)); }
+__device__ __forceinline__ f2 up2(f2 v) { return mk2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1)); }
+__device__ __forceinline__ f2 dn2(f2 v) { return mk2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1)); }
+__device__ __forceinline__ f2 ld2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
+__device__ __forceinline__ void st2(float *p, f2 v) { *reinterpret_cast<f2 *>(p) = v; }
+
+__device__ __forceinline__ float minmod1(float a, float c)
+{
+    const float mn = tmin(a, c), mx = tmax(a, c);
+    return mn > 0.0f ? mn : (mx < 0.0f ? mx : 0.0f);
+}
+__device__ __forceinline__ f2 slope2(f2 m, f2 z, f2 p)
+{
+    const f2 a = sub2(z, m), c = sub2(p, z);
+    return mk2(minmod1(a.x, c.x), minmod1(a.y, c.y));
+}
+// reconstruction of one variable: low / high face values
+__device__ __forceinline__ void recon_pair(f2 m, f2 z, f2 p, f2 &lo, f2 &hi)
+{
+    const f2 s = slope2(m, z, p);
+    lo = fma2(sc2(-0.5f), s, z);
+    hi = fma2(sc2(0.5f), s, z);
+}
+// water level with the positivity fix against the face beds blo, bhi
+__device__ __forceinline__ void recon_w_pair(f2 m, f2 z, f2 p, f2 blo, f2 bhi, f2 &lo, f2 &hi)
+{
+    const f2 s = slope2(m, z, p);
+    const f2 a = fma2(sc2(0.5f), s, z), b = fma2(sc2(-0.5f), s, z);
+    const f2 za = mul2(sc2(2.0f), z);
+    const f2 ra = sub2(za, bhi), rb = sub2(za, blo);
+    const bool hx = a.x < bhi.x, lx = !hx && b.x < blo.x;
+    const bool hy = a.y < bhi.y, ly = !hy && b.y < blo.y;
+    hi = mk2(hx ? bhi.x : (lx ? rb.x : a.x), hy ? bhi.y : (ly ? rb.y : a.y));
+    lo = mk2(hx ? ra.x : (lx ? blo.x : b.x), hy ? ra.y : (ly ? blo.y : b.y));
+}
+
+struct FS2 {
+    f2 h, u, v, c;
+};
+__device__ __forceinline__ FS2 face_pair(f2 wf, f2 Pf, f2 Qf, f2 bf, float g, float eps)
+{
+    FS2 s;
+    s.h = max2(sub2(wf, bf), sc2(0.0f));
+    const f2 h2 = mul2(s.h, s.h), h4 = mul2(h2, h2);
+    const f2 den = add2(h4, max2(h4, sc2(eps)));
+    const f2 iv = mul2(mul2(sc2((float)BSQ_SQRT2), s.h), mk2(trsqrt(den.x), trsqrt(den.y)));
+    s.u = mul2(iv, Pf);
+    s.v = mul2(iv, Qf);
+    const f2 gh = mul2(sc2(g), s.h);
+    s.c = mk2(tsqrt(gh.x), tsqrt(gh.y));
+    return s;
+}
+// central-upwind flux (Eq. 5) on a pair of faces of one direction
+template <int DIR>
+__device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f2 &H0, f2 &H1, f2 &H2)
+{
+    const f2 unL = DIR == 0 ? L.u : L.v, unR = DIR == 0 ? R.u : R.v;
+    const f2 ap = max2(max2(add2(unL, L.c), add2(unR, R.c)), sc2(0.0f));
+    const f2 am = min2(min2(sub2(unL, L.c), sub2(unR, R.c)), sc2(0.0f));
+    const f2 den = sub2(ap, am);
+    const bool mvx = den.x > 0.0f, mvy = den.y > 0.0f;
+    const f2 inv = mk2(trcp(mvx ? den.x : 1.0f), trcp(mvy ? den.y : 1.0f));
+    const f2 pL = mul2(L.h, L.u), qL = mul2(L.h, L.v), pR = mul2(R.h, R.u), qR = mul2(R.h, R.v);
+    const f2 hg = sc2(0.5f * g);
+    const f2 hhL = mul2(mul2(hg, L.h), L.h), hhR = mul2(mul2(hg, R.h), R.h);
+    f2 FL0, FL1, FL2, FR0, FR1, FR2;
+    if (DIR == 0) {
+        FL0 = pL; FL1 = fma2(pL, L.u, hhL); FL2 = mul2(qL, L.u);
+        FR0 = pR; FR1 = fma2(pR, R.u, hhR); FR2 = mul2(qR, R.u);
+    } else {
+        FL0 = qL; FL1 = mul2(pL, L.v); FL2 = fma2(qL, L.v, hhL);
+        FR0 = qR; FR1 = mul2(pR, R.v); FR2 = fma2(qR, R.v, hhR);
+    }
+    const f2 k = mul2(mul2(ap, am), inv);
+    const f2 nam = mul2(am, sc2(-1.0f));
+    const f2 t0 = fma2(k, sub2(R.h, L.h), mul2(fma2(nam, FR0, mul2(ap, FL0)), inv));
+    const f2 t1 = fma2(k, sub2(pR, pL), mul2(fma2(nam, FR1, mul2(ap, FL1)), inv));
+    const f2 t2 = fma2(k, sub2(qR, qL), mul2(fma2(nam, FR2, mul2(ap, FL2)), inv));
+    H0 = mk2(mvx ? t0.x : 0.0f, mvy ? t0.y : 0.0f);
+    H1 = mk2(mvx ? t1.x : 0.0f, mvy ? t1.y : 0.0f);
+    H2 = mk2(mvx ? t2.x : 0.0f, mvy ? t2.y : 0.0f);
+}
+
+constexpr int SW2_COLS = 60;  // interior columns per warp strip (two per lane, lanes 1..30)
+
+template <int ROWS, int YS>
+__device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int nstrip)
+{
+    typedef float T;
+    const Coef cf = *D.coef;
+    if (!cf.active) return;
+    const int lane = threadIdx.x & 31;
+    const int wg = blk * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int strip = wg % nstrip, band = wg / nstrip;
+    const int nx = D.nx, ny = D.ny;
+    const int j0 = band * ROWS;
+    if (j0 >= ny) return;
+    const int c0 = strip * SW2_COLS - 2 + 2 * lane;  // this lane's columns c0, c0 + 1
+    const bool inner = lane >= 1 && lane <= 30;
+    const bool out0 = inner && c0 < nx, out1 = inner && c0 + 1 < nx;
+    const int kc0 = min(c0, nx + 2), kc1 = min(c0 + 1, nx + 2), kc2 = min(c0 + 2, nx + 2);
+    const T *w = D.w[cf.wc];
+    const float g = D.g, eps = D.eps;
+    const float rdx = D.rdx, rdy = D.rdy;
+    const float half_rdx = 0.5f * rdx, half_rdy = 0.5f * rdy;
+    const float rdx2 = rdx * rdx, rdy2 = rdy * rdy, q_rdxy = 0.25f * rdx * rdy;
+    const float c_xxx = 0.5f * rdx2 * rdx, c_yyy = 0.5f * rdy2 * rdy;
+    const float Bg = D.Bd * g, kB = D.Bd + 1.0f / 3.0f, sixth = 1.0f / 6.0f;
+    const float b0c = cf.betaf[0], b1c = cf.betaf[1], b2c = cf.betaf[2];
+    const float g0c = cf.gamf[0], g1c = cf.gamf[1], g2c = cf.gamf[2];
+    T *H = D.hist;
+    const T *corner = D.corner;
+    const int cp = D.cpitch;
+    const int pitch = D.pitch, hx = D.hx;
+    const int ifs = (int)D.fstride, s0o = cf.s0 * ifs, s1o = cf.s1 * ifs, s2o = cf.s2 * ifs;
+
+    f2 wW[4], PW[4], QW[4], eW[5], dW[4], bW[3], KW[4], KRW[4];
+#pragma unroll
+    for (int q = 0; q < 5; q++) eW[q] = sc2(0.0f);
+#pragma unroll
+    for (int q = 0; q < 4; q++) { wW[q] = PW[q] = QW[q] = dW[q] = KW[q] = KRW[q] = sc2(0.0f); }
+#pragma unroll
+    for (int q = 0; q < 3; q++) bW[q] = sc2(0.0f);
+    FS2 Nprev = {sc2(0.0f), sc2(0.0f), sc2(0.0f), sc2(0.0f)};
+    f2 Hy0 = sc2(0.0f), Hy1 = sc2(0.0f), Hy2 = sc2(0.0f);
+    {
+        const int rr = min(j0 - 2, ny + 2);
+        const T *kr = corner + (long long)(rr + 2) * cp + 2;
+        const float k0 = kr[kc0], k1 = kr[kc1], k2 = kr[kc2];
+        KW[3] = mk2(k0, k1);
+        KRW[3] = mk2(k1, k2);
+    }
+    unsigned long long nclamp = 0;
+    const int rend = min(j0 + ROWS, ny) + 2;
+    f2 pw, pP, pQ, pK, pKR;
+    auto load_lead = [&](int r) {
+        const int rr = min(r, ny + 1);
+        const int cr = (rr + 2) * pitch + c0 + hx;
+        pw = ld2(w + cr); pP = ld2(D.P + cr); pQ = ld2(D.Q + cr);
+        const int kr = min(r + 1, ny + 2);
+        const T *kp = corner + (long long)(kr + 2) * cp + 2;
+        const float k0 = kp[kc0], k1 = kp[kc1], k2 = kp[kc2];
+        pK = mk2(k0, k1);
+        pKR = mk2(k1, k2);
+    };
+    f2 hE1 = sc2(0.0f), hF1 = hE1, hG1 = hE1, hGs1 = hE1, hE2 = hE1, hF2 = hE1, hG2 = hE1, hGs2 = hE1, hcw = hE1;
+    f2 hym = hE1, hye = hE1, hyc = hE1;
+    f2 yt = sc2(0.0f), yPi = sc2(1.0f), yal0 = sc2(0.0f), yal1 = sc2(0.0f), ybe = sc2(1.0f);
+    const int ynch = YS > 0 ? ychunk_stride((ny + YS - 1) / YS) : 0;
+    const long long ys_s = (long long)nx * ynch;
+    auto load_hist = [&](int o) {
+        if (out0 && o >= j0 && o < ny) {
+            const int c = (o + 2) * pitch + c0 + hx;
+            hcw = ld2(D.cw + c);
+            const T *h1 = H + (s1o + c), *h2 = H + (s2o + c);
+            hE1 = ld2(h1); hF1 = ld2(h1 + 3 * ifs); hG1 = ld2(h1 + 6 * ifs); hGs1 = ld2(h1 + 12 * ifs);
+            hE2 = ld2(h2); hF2 = ld2(h2 + 3 * ifs); hG2 = ld2(h2 + 6 * ifs); hGs2 = ld2(h2 + 12 * ifs);
+            if (YS > 0) { hym = ld2(D.fym + c); hye = ld2(D.fye + c); hyc = ld2(D.fyc + c); }
+        }
+    };
+    load_lead(j0 - 2);
+    for (int r = j0 - 2; r < rend; r++) {
+        const f2 wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR;
+        const f2 cE1 = hE1, cF1 = hF1, cG1 = hG1, cGs1 = hGs1, cE2 = hE2, cF2 = hF2, cG2 = hG2, cGs2 = hGs2;
+        const f2 ccw = hcw, cym = hym, cye = hye, cyc = hyc;
+        if (r + 1 < rend) load_lead(r + 1);
+        load_hist(r - 1);
+#pragma unroll
+        for (int q = 0; q < 3; q++) { wW[q] = wW[q + 1]; PW[q] = PW[q + 1]; QW[q] = QW[q + 1]; dW[q] = dW[q + 1]; KW[q] = KW[q + 1]; KRW[q] = KRW[q + 1]; }
+#pragma unroll
+        for (int q = 0; q < 4; q++) eW[q] = eW[q + 1];
+        bW[0] = bW[1]; bW[1] = bW[2];
+        wW[3] = wn; PW[3] = Pn; QW[3] = Qn; KW[3] = Kn; KRW[3] = KRn;
+        {
+            const f2 half = sc2(0.5f);
+            const f2 bw_ = mul2(half, add2(KW[2], KW[3])), be_ = mul2(half, add2(KRW[2], KRW[3]));
+            const f2 bs_ = mul2(half, add2(KW[2], KRW[2])), bn_ = mul2(half, add2(KW[3], KRW[3]));
+            const f2 bc = mul2(sc2(0.25f), add2(add2(add2(bw_, be_), bs_), bn_));
+            const f2 d = max2(sub2(sc2(D.w_s), bc), sc2(0.0f));
+            bW[2] = bc;
+            dW[3] = d;
+            eW[4] = sub2(max2(sub2(wn, bc), sc2(0.0f)), d);
+        }
+        // y-reconstruction of row r-1, y-face flux between rows r-2 and r-1
+        const f2 bS = mul2(sc2(0.5f), add2(KW[1], KRW[1])), bN = mul2(sc2(0.5f), add2(KW[2], KRW[2]));
+        f2 wl, wh, Pl, Ph, Ql, Qh;
+        recon_w_pair(wW[1], wW[2], wW[3], bS, bN, wl, wh);
+        recon_pair(PW[1], PW[2], PW[3], Pl, Ph);
+        recon_pair(QW[1], QW[2], QW[3], Ql, Qh);
+        const FS2 S = face_pair(wl, Pl, Ql, bS, g, eps);
+        const FS2 Nn = face_pair(wh, Ph, Qh, bN, g, eps);
+        f2 h0, h1, h2;
+        flux_pair<1>(Nprev, S, g, h0, h1, h2);
+        // ---- finish row o = r - 2
+        const int o = r - 2;
+        const f2 w0 = wW[1], P0 = PW[1], Q0 = QW[1];
+        // x-neighbours: own pair and the pairs of lanes L-1 (m) and L+1 (p)
+        const f2 wLm = up2(w0), wLp = dn2(w0), PLm = up2(P0), PLp = dn2(P0), QLm = up2(Q0), QLp = dn2(Q0);
+        const f2 wm = mk2(wLm.y, w0.x), wp = mk2(w0.y, wLp.x);
+        const f2 Pm = mk2(PLm.y, P0.x), Pp = mk2(P0.y, PLp.x);
+        const f2 Qm = mk2(QLm.y, Q0.x), Qp = mk2(Q0.y, QLp.x);
+        const f2 bxW = mul2(sc2(0.5f), add2(KW[0], KW[1])), bxE = mul2(sc2(0.5f), add2(KRW[0], KRW[1]));
+        f2 xwl, xwh, xPl, xPh, xQl, xQh;
+        recon_w_pair(wm, w0, wp, bxW, bxE, xwl, xwh);
+        recon_pair(Pm, P0, Pp, xPl, xPh);
+        recon_pair(Qm, Q0, Qp, xQl, xQh);
+        const FS2 Wst = face_pair(xwl, xPl, xQl, bxW, g, eps);
+        const FS2 Est = face_pair(xwh, xPh, xQh, bxE, g, eps);
+        // E state of the column to the left: lane L-1's second column, own first
+        FS2 El;
+        El.h = mk2(__shfl_up_sync(0xffffffffu, Est.h.y, 1), Est.h.x);
+        El.u = mk2(__shfl_up_sync(0xffffffffu, Est.u.y, 1), Est.u.x);
+        El.v = mk2(__shfl_up_sync(0xffffffffu, Est.v.y, 1), Est.v.x);
+        El.c = mk2(__shfl_up_sync(0xffffffffu, Est.c.y, 1), Est.c.x);
+        f2 x0, x1, x2;
+        flux_pair<0>(El, Wst, g, x0, x1, x2);  // faces c - 1/2
+        const f2 xe0 = mk2(x0.y, __shfl_down_sync(0xffffffffu, x0.x, 1));  // faces c + 1/2
+        const f2 xe1 = mk2(x1.y, __shfl_down_sync(0xffffffffu, x1.x, 1));
+        const f2 xe2 = mk2(x2.y, __shfl_down_sync(0xffffffffu, x2.x, 1));
+        // neighbours for the dispersive and cross terms
+        const f2 e0 = eW[2];
+        const f2 eLm = up2(e0), eLp = dn2(e0);
+        const f2 em1 = mk2(eLm.y, e0.x), ep1 = mk2(e0.y, eLp.x), em2 = eLm, ep2 = eLp;
+        const f2 eS = eW[1], eN = eW[3];
+        const float eSLm = __shfl_up_sync(0xffffffffu, eS.y, 1), eSLp = __shfl_down_sync(0xffffffffu, eS.x, 1);
+        const float eNLm = __shfl_up_sync(0xffffffffu, eN.y, 1), eNLp = __shfl_down_sync(0xffffffffu, eN.x, 1);
+        const f2 eSm = mk2(eSLm, eS.x), eSp = mk2(eS.y, eSLp), eNm = mk2(eNLm, eN.x), eNp = mk2(eN.y, eNLp);
+        const f2 dd = dW[1];
+        const f2 dm = mk2(__shfl_up_sync(0xffffffffu, dd.y, 1), dd.x), dp = mk2(dd.y, __shfl_down_sync(0xffffffffu, dd.x, 1));
+        const f2 QS = QW[0], QN = QW[2], PS = PW[0], PN = PW[2];
+        const f2 QSm = mk2(__shfl_up_sync(0xffffffffu, QS.y, 1), QS.x), QSp = mk2(QS.y, __shfl_down_sync(0xffffffffu, QS.x, 1));
+        const f2 QNm = mk2(__shfl_up_sync(0xffffffffu, QN.y, 1), QN.x), QNp = mk2(QN.y, __shfl_down_sync(0xffffffffu, QN.x, 1));
+        const f2 PSm = mk2(__shfl_up_sync(0xffffffffu, PS.y, 1), PS.x), PSp = mk2(PS.y, __shfl_down_sync(0xffffffffu, PS.x, 1));
+        const f2 PNm = mk2(__shfl_up_sync(0xffffffffu, PN.y, 1), PN.x), PNp = mk2(PN.y, __shfl_down_sync(0xffffffffu, PN.x, 1));
+        const bool valid = (out0 || out1) && o >= j0 && o < ny;
+        {
+            const f2 srdx = sc2(rdx), srdy = sc2(rdy);
+            const f2 divx0 = mul2(sub2(xe0, x0), srdx), divx1 = mul2(sub2(xe1, x1), srdx), divx2 = mul2(sub2(xe2, x2), srdx);
+            const f2 divy0 = mul2(sub2(h0, Hy0), srdy), divy1 = mul2(sub2(h1, Hy1), srdy), divy2 = mul2(sub2(h2, Hy2), srdy);
+            const f2 bS0 = mul2(sc2(0.5f), add2(KW[0], KRW[0])), bN0 = mul2(sc2(0.5f), add2(KW[1], KRW[1]));
+            const f2 bc = bW[0];
+            const f2 ng = sc2(-g);
+            const f2 srcx = mul2(mul2(mul2(ng, sub2(bxE, bxW)), srdx), fma2(sc2(-0.5f), add2(bxE, bxW), w0));
+            const f2 srcy = mul2(mul2(mul2(ng, sub2(bN0, bS0)), srdy), fma2(sc2(-0.5f), add2(bN0, bS0), w0));
+            const f2 d = dd;
+            const f2 ddx = mul2(sub2(dp, dm), sc2(half_rdx));
+            const f2 ddy = mul2(sub2(dW[2], dW[0]), sc2(half_rdy));
+            const f2 m2 = sc2(-2.0f), p2 = sc2(2.0f);
+            const f2 e_xx = mul2(add2(fma2(m2, e0, ep1), em1), sc2(rdx2));
+            const f2 e_yy = mul2(add2(fma2(m2, e0, eW[3]), eW[1]), sc2(rdy2));
+            const f2 e_xy = mul2(add2(sub2(sub2(eNp, eSp), eNm), eSm), sc2(q_rdxy));
+            const f2 e_xxx = mul2(sub2(fma2(p2, em1, fma2(m2, ep1, ep2)), em2), sc2(c_xxx));
+            const f2 e_yyy = mul2(sub2(fma2(p2, eW[1], fma2(m2, eW[3], eW[4])), eW[0]), sc2(c_yyy));
+            const f2 eyy_p = mul2(add2(fma2(m2, ep1, eNp), eSp), sc2(rdy2));
+            const f2 eyy_m = mul2(add2(fma2(m2, em1, eNm), eSm), sc2(rdy2));
+            const f2 exx_p = mul2(add2(fma2(m2, eW[3], eNp), eNm), sc2(rdx2));
+            const f2 exx_m = mul2(add2(fma2(m2, eW[1], eSp), eSm), sc2(rdx2));
+            const f2 e_xyy = mul2(sub2(eyy_p, eyy_m), sc2(half_rdx));
+            const f2 e_xxy = mul2(sub2(exx_p, exx_m), sc2(half_rdy));
+            const f2 Bgd2 = mul2(mul2(sc2(Bg), d), d), Bgd3 = mul2(Bgd2, d);
+            const f2 dispx = fma2(Bgd3, add2(e_xxx, e_xyy), mul2(Bgd2, fma2(ddx, fma2(p2, e_xx, e_yy), mul2(ddy, e_xy))));
+            const f2 dispy = fma2(Bgd3, add2(e_yyy, e_xxy), mul2(Bgd2, fma2(ddy, fma2(p2, e_yy, e_xx), mul2(ddx, e_xy))));
+            const f2 E = sub2(mul2(divx0, sc2(-1.0f)), divy0);
+            const f2 F = add2(add2(sub2(mul2(divx1, sc2(-1.0f)), divy1), srcx), dispx);
+            const f2 G = add2(add2(sub2(mul2(divx2, sc2(-1.0f)), divy2), srcy), dispy);
+            const f2 Q_x = mul2(sub2(Qp, Qm), sc2(half_rdx));
+            const f2 Q_y = mul2(sub2(QW[2], QW[0]), sc2(half_rdy));
+            const f2 Q_xy = mul2(add2(sub2(sub2(QNp, QSp), QNm), QSm), sc2(q_rdxy));
+            const f2 P_x = mul2(sub2(Pp, Pm), sc2(half_rdx));
+            const f2 P_y = mul2(sub2(PW[2], PW[0]), sc2(half_rdy));
+            const f2 P_xy = mul2(add2(sub2(sub2(PNp, PSp), PNm), PSm), sc2(q_rdxy));
+            const f2 dsx = mul2(mul2(d, ddx), sc2(sixth)), dsy = mul2(mul2(d, ddy), sc2(sixth));
+            const f2 kBd2 = mul2(mul2(sc2(kB), d), d);
+            const f2 Fs = fma2(kBd2, Q_xy, fma2(dsy, Q_x, mul2(dsx, Q_y)));
+            const f2 Gs = fma2(kBd2, P_xy, fma2(dsx, P_y, mul2(dsy, P_x)));
+            // AB3 / Euler combine (Eqs. 42-43), both history levels read
+            f2 dw = mul2(sc2(b0c), E), dU = mul2(sc2(b0c), F), dV = fma2(sc2(g0c), Gs, mul2(sc2(b0c), G));
+            dw = fma2(sc2(b1c), cE1, dw);
+            dU = fma2(sc2(b1c), cF1, dU);
+            dV = add2(dV, fma2(sc2(g1c), cGs1, mul2(sc2(b1c), cG1)));
+            dw = fma2(sc2(b2c), cE2, dw);
+            dU = fma2(sc2(b2c), cF2, dU);
+            dV = add2(dV, fma2(sc2(g2c), cGs2, mul2(sc2(b2c), cG2)));
+            dU = sub2(dU, Fs);  // F*(Q^{n+1}) is added by the x-line kernel
+            const f2 y = sub2(dw, ccw);
+            f2 wnew = add2(w0, y);
+            f2 cwn = sub2(sub2(wnew, w0), y);
+            const bool clx = wnew.x < bc.x, cly = wnew.y < bc.y;
+            wnew = mk2(clx ? bc.x : wnew.x, cly ? bc.y : wnew.y);
+            cwn = mk2(clx ? 0.0f : cwn.x, cly ? 0.0f : cwn.y);
+            nclamp += (valid && out0 && clx ? 1ull : 0ull) + (valid && out1 && cly ? 1ull : 0ull);
+            if (valid) {
+                const int ci = (o + 2) * pitch + c0 + hx;
+                T *hp = H + (s0o + ci);
+                T *wp_ = D.w[cf.wc ^ 1] + ci;
+                if (out1) {
+                    st2(hp, E); st2(hp + 3 * ifs, F); st2(hp + 6 * ifs, G); st2(hp + 12 * ifs, Gs);
+                    st2(wp_, wnew); st2(D.cw + ci, cwn); st2(D.dU + ci, dU); st2(D.dV + ci, dV);
+                } else {
+                    hp[0] = E.x; hp[3 * ifs] = F.x; hp[6 * ifs] = G.x; hp[12 * ifs] = Gs.x;
+                    *wp_ = wnew.x; D.cw[ci] = cwn.x; D.dU[ci] = dU.x; D.dV[ci] = dV.x;
+                }
+                if (YS > 0) {
+                    // the chunk summaries of k_ysum, per column
+                    f2 rr = dV;
+                    if (o == 0) rr = add2(rr, mk2(D.corrS[c0], out1 ? D.corrS[c0 + 1] : 0.0f));
+                    if (o == ny - 1) rr = add2(rr, mk2(D.corrN[c0], out1 ? D.corrN[c0 + 1] : 0.0f));
+                    yt = fma2(cym, rr, mul2(cye, yt));
+                    yPi = mul2(cye, yPi);
+                    yal0 = fma2(ybe, yt, yal0);
+                    yal1 = fma2(ybe, yPi, yal1);
+                    ybe = mul2(mul2(cyc, sc2(-1.0f)), ybe);
+                    if ((o + 1) % YS == 0 || o == ny - 1) {
+                        const int kk = o / YS;
+                        T *sums = D.ysums;
+                        const long long so0 = (long long)c0 * ynch + kk;
+                        sums[so0] = yPi.x; sums[ys_s + so0] = yt.x; sums[2 * ys_s + so0] = yal0.x;
+                        sums[3 * ys_s + so0] = yal1.x; sums[4 * ys_s + so0] = ybe.x;
+                        if (out1) {
+                            const long long so1 = so0 + ynch;
+                            sums[so1] = yPi.y; sums[ys_s + so1] = yt.y; sums[2 * ys_s + so1] = yal0.y;
+                            sums[3 * ys_s + so1] = yal1.y; sums[4 * ys_s + so1] = ybe.y;
+                        }
+                        yt = sc2(0.0f); yPi = sc2(1.0f); yal0 = sc2(0.0f); yal1 = sc2(0.0f); ybe = sc2(1.0f);
+                    }
+                }
+            }
+        }
+        Nprev = Nn;
+        Hy0 = h0; Hy1 = h1; Hy2 = h2;
+    }
+    for (int s = 16; s > 0; s >>= 1) nclamp += __shfl_xor_sync(0xffffffffu, nclamp, s);
+    if (lane == 0 && nclamp) atomicAdd(&D.ctl->clamps, nclamp);
+    if (blk == 0 && threadIdx.x == 0) {
+        Ctl *ct = D.ctl;
+        ct->dtm2 = ct->dtm1;
+        ct->dtm1 = cf.dt;
+        ct->last_dt = cf.dt;
+        ct->t = cf.t1;
+        ct->n = cf.n + 1;
+        ct->rate_bits = 0ull;
+    }
+}
+
+template <int ROWS, int YS>
+__global__ void __launch_bounds__(128, 2) k_rhs_sw2(Dev<float> D, int nstrip)
+{
+    rhs_sw2_body<ROWS, YS>(D, blockIdx.x, nstrip);
+}
+
 // ------------------------------------------------------------------ y-line solves
 
 // Thread (column c, chunk k) owns rows [k*KCH, (k+1)*KCH) of one column.
@@ -2916,6 +3287,25 @@ cudaError_t configure(int nx)
     return e;
 }
 
+// two-columns-per-lane RHS (single precision, default configuration)
+static bool launch_rhs2(const Dev<float> &D, cudaStream_t st, int rows, int ky)
+{
+    const int nstrip = (D.nx + SW2_COLS - 1) / SW2_COLS;
+    const int nband = (D.ny + rows - 1) / rows;
+    const int blocks = (int)(((long long)nstrip * nband + 3) / 4);
+    if (rows == 32) {
+        if (ky == 16) k_rhs_sw2<32, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+        else if (ky == 8) k_rhs_sw2<32, 8><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw2<32, 0><<<blocks, 128, 0, st>>>(D, nstrip);
+    } else {
+        if (ky == 16) k_rhs_sw2<64, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+        else if (ky == 8) k_rhs_sw2<64, 8><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw2<64, 0><<<blocks, 128, 0, st>>>(D, nstrip);
+    }
+    return true;
+}
+static bool launch_rhs2(const Dev<double> &, cudaStream_t, int, int) { return false; }
+
 // x-solver variants (tune_xtma): 0 automatic -- the two-group kernel in
 // single precision where a row takes at most 256 threads of K = 4 or 8
 // elements and both staging buffers fit, else the one-row persistent kernel,
@@ -2971,7 +3361,10 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
                           (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
         ysum_fused = fast && D.ysplit && rows != 16 && D.tune_ysum == 0;
         const bool t1 = D.theta == (T)1;
-        if (fast && ysum_fused) {
+        const bool pair2 = fast && sizeof(T) == 4 && D.tune_rhs1 == 0 && rows != 16;
+        if (pair2) {
+            launch_rhs2(D, st, rows, ysum_fused ? ysplit_rows<T>(D.tune_yk) : 0);
+        } else if (fast && ysum_fused) {
             const int KY = ysplit_rows<T>(D.tune_yk);
             if (rows == 32) {
                 if (KY == 16) k_rhs_sw<T, 32, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
