@@ -91,13 +91,16 @@ typedef struct {
                               [2] bit 0: RHS kernel (0 sliding window, 1 shared-memory tiles),
                               bit 1: x-solver without shared-memory staging, bit 2: x-solver
                               with two rows in flight per block, bit 3: persistent x-solver
-                              with one row in flight; [3] rows per warp
+                              with one row in flight, bit 4: x-solver with one warp per row
+                              (the single-precision default); [3] rows per warp
                               of the sliding window (16, 32, 64); [4] x-solver elements per
                               thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
                               y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
                               of their own instead of inside the RHS kernel, bit 1: one column
                               per lane in the single-precision RHS kernel (instead of two,
-                              paired); [7] reserved */
+                              paired); [7] bit 0: paired RHS kernel at three blocks per
+                              multiprocessor, bit 1: F*(Q^{n+1}) by its own pass before a
+                              lighter warp-per-row x-solver */
 } bsq_params;
 
 typedef struct {

@@ -368,6 +368,8 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
+    D.tune_rhs2 = p.tune[7] & 1;
+    D.tune_xws = (p.tune[7] >> 1) & 1;
     D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
@@ -1128,7 +1130,7 @@ extern "C" bsq_status bsq_restore(bsq_domain *d, const void *buf, size_t len)
 
 // ------------------------------------------------------------------ profiling
 
-static const char *kKernelNames[] = {"ghost", "rhs_combine", "ysolve", "ghost_q", "xsolve"};
+static const char *kKernelNames[] = {"ghost", "rhs_combine", "ysolve", "xrhs", "xsolve"};
 
 extern "C" const char *bsq_kernel_name(int k)
 {
@@ -1170,11 +1172,5 @@ extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, doub
 extern "C" int bsq_launches_per_step(const bsq_domain *d)
 {
     if (!d) return 0;
-    const int ysplit = d->fp64 ? d->Dd.ysplit : d->Df.ysplit;
-    const int nx = d->nx;
-    int tma;
-    if (d->fp64) tma = xsolver_staged<double>(d->Dd, nx);
-    else tma = xsolver_staged<float>(d->Df, nx);
-    const int cross = d->p.cross_mode != 0;
-    return 1 /* ghost */ + 1 /* rhs */ + (ysplit ? 3 : 1) + ((cross && !tma) ? 1 : 0) + 1 /* x-solver */;
+    return d->fp64 ? step_launches<double>(d->Dd) : step_launches<float>(d->Df);
 }

@@ -16,6 +16,7 @@ template <typename T> cudaError_t configure(int nx);
 template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
 template <typename T> int xsolver_staged(const Dev<T> &D, int nx);
+template <typename T> int step_launches(const Dev<T> &D);
 template <typename T> cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt);
 template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, int wc);
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
