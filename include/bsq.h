@@ -98,9 +98,7 @@ typedef struct {
                               y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
                               of their own instead of inside the RHS kernel, bit 1: one column
                               per lane in the single-precision RHS kernel (instead of two,
-                              paired); [7] bit 0: paired RHS kernel at three blocks per
-                              multiprocessor, bit 1: F*(Q^{n+1}) by its own pass before a
-                              lighter warp-per-row x-solver */
+                              paired); [7] reserved */
 } bsq_params;
 
 typedef struct {

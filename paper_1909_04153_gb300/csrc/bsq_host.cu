@@ -368,8 +368,6 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
-    D.tune_rhs2 = p.tune[7] & 1;
-    D.tune_xws = (p.tune[7] >> 1) & 1;
     D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;

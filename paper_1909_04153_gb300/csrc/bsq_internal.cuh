@@ -61,8 +61,6 @@ struct Dev {
     int ysplit;                    // 1: three-launch y-solver (summaries, scans, apply)
     int tune_ysum;                 // 1: chunk summaries by their own kernel, not in the RHS kernel
     int tune_rhs1;                 // 1: one column per lane in the sliding-window RHS (single precision)
-    int tune_rhs2;                 // bit 0: paired RHS kernel at 3 blocks per multiprocessor, no history prefetch
-    int tune_xws;                  // 1: warp-per-row x-solver with chunks staged by bulk copies
     T *ysums, *yin, *yxa;          // its chunk summaries (5 per chunk) and scanned values
     int bc[4];
     // controller inputs (FP64)

@@ -15,8 +15,9 @@
 //               P, the Eq. 22 rate of the new state, and in its last block the
 //               controller of the next step (Eqs. 22, 47, 42, 44-46)
 //
-// Other kernel shapes (tiled RHS, block-scan y-solver, TMA-staged x-solvers,
-// a separate F* pass) are selected by bsq_params.tune and parity-tested.
+// Other kernel shapes (tiled or one-column-per-lane RHS, block-scan
+// y-solver, TMA-staged x-solvers) are selected by bsq_params.tune and
+// parity-tested.
 // Fields are SoA, row-major, x fastest, with a 2-cell halo in y and a 16-byte
 // aligned halo in x, so rows can be read as float4 / double2.
 #include <cuda_runtime.h>
@@ -1229,10 +1230,7 @@ __device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f
 
 constexpr int SW2_COLS = 60;  // interior columns per warp strip (two per lane, lanes 1..30)
 
-// PFH: the history of the row finished next is loaded one iteration ahead
-// (more registers, fewer exposed loads); without it the loads are issued at
-// the top of the iteration that uses them.
-template <int YS, bool PFH>
+template <int YS>
 __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int nstrip, int ROWS)
 {
     typedef float T;
@@ -1310,11 +1308,10 @@ __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int n
     load_lead(j0 - 2);
     for (int r = j0 - 2; r < rend; r++) {
         const f2 wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR;
-        if (!PFH) load_hist(r - 2);
         const f2 cE1 = hE1, cF1 = hF1, cG1 = hG1, cGs1 = hGs1, cE2 = hE2, cF2 = hF2, cG2 = hG2, cGs2 = hGs2;
         const f2 ccw = hcw, cym = hym, cye = hye, cyc = hyc;
         if (r + 1 < rend) load_lead(r + 1);
-        if (PFH) load_hist(r - 1);
+        load_hist(r - 1);
 #pragma unroll
         for (int q = 0; q < 3; q++) { wW[q] = wW[q + 1]; PW[q] = PW[q + 1]; QW[q] = QW[q + 1]; dW[q] = dW[q + 1]; KW[q] = KW[q + 1]; KRW[q] = KRW[q + 1]; }
 #pragma unroll
@@ -1492,12 +1489,11 @@ __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int n
     }
 }
 
-// MB blocks of 4 warps per multiprocessor: 2 with the history prefetch
-// (up to 255 registers), 3 without it (168 registers)
-template <int YS, int MB>
-__global__ void __launch_bounds__(128, MB) k_rhs_sw2(Dev<float> D, int nstrip, int rows)
+// two blocks of 4 warps per multiprocessor (up to 255 registers a thread)
+template <int YS>
+__global__ void __launch_bounds__(128, 2) k_rhs_sw2(Dev<float> D, int nstrip, int rows)
 {
-    rhs_sw2_body<YS, MB == 2>(D, blockIdx.x, nstrip, rows);
+    rhs_sw2_body<YS>(D, blockIdx.x, nstrip, rows);
 }
 
 // ------------------------------------------------------------------ y-line solves
@@ -1753,29 +1749,34 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
     if (i >= nx || k >= nch) return;
     const int j0 = k * KY;
     const long long bo = (long long)i * ychunk_stride(nch) + k;
-    // every load of both sweeps is issued before any arithmetic, so they overlap
-    T rr[KY], mm[KY], ee[KY], cc[KY], Qo[KY], cq[KY];
-    const T y0 = yin[bo], x0 = xaft[bo];
+    // all loads of a phase are issued before any store, so they overlap
+    T rr[KY], mm[KY], ee[KY];
 #pragma unroll
     for (int q = 0; q < KY; q++) {
         const int j = j0 + q;
         const bool v = j < ny;
         const long long o = v ? fidx(D, i, j) : 0;
-        rr[q] = v ? D.dV[o] : (T)0;
+        T r = v ? D.dV[o] : (T)0;
+        if (j == 0) r += D.corrS[i];
+        if (j == ny - 1) r += D.corrN[i];
+        rr[q] = r;
         mm[q] = v ? D.fym[o] : (T)0;
         ee[q] = v ? D.fye[o] : (T)1;
+    }
+    T y = yin[bo];
+#pragma unroll
+    for (int q = 0; q < KY; q++) { y = mm[q] * rr[q] + ee[q] * y; rr[q] = y; }
+    T cc[KY], Qo[KY], cq[KY];
+#pragma unroll
+    for (int q = 0; q < KY; q++) {
+        const int j = j0 + q;
+        const bool v = j < ny;
+        const long long o = v ? fidx(D, i, j) : 0;
         cc[q] = v ? D.fyc[o] : (T)0;
         Qo[q] = v ? D.Q[o] : (T)0;
         cq[q] = (v && D.kahan) ? D.cQ[o] : (T)0;
     }
-    if (j0 == 0) rr[0] += D.corrS[i];
-#pragma unroll
-    for (int q = 0; q < KY; q++)
-        if (j0 + q == ny - 1) rr[q] += D.corrN[i];
-    T y = y0;
-#pragma unroll
-    for (int q = 0; q < KY; q++) { y = mm[q] * rr[q] + ee[q] * y; rr[q] = y; }
-    T x = x0;
+    T x = xaft[bo];
     const T gxi = D.gx[i];
 #pragma unroll
     for (int q = KY - 1; q >= 0; q--) {
@@ -3118,238 +3119,6 @@ static size_t xtma_smem(int span, int hx)
     return ((size_t)XT_ARR_PLAIN * span + (size_t)XT_ARR_HALO * (span + 2 * hx)) * sizeof(T);
 }
 
-// ---- F*(Q^{n+1}) of the x-line right-hand side, by its own stencil pass
-//
-// Sequential cross form: U* receives F*(Q^{n+1}) with Q^{n+1} just solved
-// (Eq. 14).  One thread per cell adds F*(Q^{n+1}) and the maker corrections
-// of the row ends (-A (g^{n+1} - g^n), Eq. 19 in increment form) to dU, so the
-// x-line solver that follows reads its right-hand side whole.  Q^{n+1} at the
-// ghost cells is taken as in the x-solvers: maker values at t_{n+1} on maker
-// sides, the even mirror across W/E walls (Q is tangential there) and the odd
-// mirror across S/N walls, corners from the W/E-patched row.
-//   F* = (1/6) d (d_x Q_y + d_y Q_x) + (B + 1/3) d^2 Q_xy
-// with centred differences, evaluated as d (c1 (dd_x dQ_y + dd_y dQ_x) + c2 d dQ_xy).
-template <typename T>
-__device__ __forceinline__ T qn1_x(const Dev<T> &D, int i, int j)  // 0 <= j < ny, -1 <= i <= nx
-{
-    if (i < 0) return D.bc[SW] == MAKER ? D.mqW[j] : D.Q[fidx(D, 0, j)];
-    if (i >= D.nx) return D.bc[SE] == MAKER ? D.mqE[j] : D.Q[fidx(D, D.nx - 1, j)];
-    return D.Q[fidx(D, i, j)];
-}
-template <typename T>
-__device__ __forceinline__ T qn1_xy(const Dev<T> &D, int i, int j)  // -1 <= i <= nx, -1 <= j <= ny
-{
-    if (j < 0) return D.bc[SS] == MAKER ? D.mqS[min(max(i, -1), D.nx) + 1] : -qn1_x(D, i, 0);
-    if (j >= D.ny) return D.bc[SN] == MAKER ? D.mqN[min(max(i, -1), D.nx) + 1] : -qn1_x(D, i, D.ny - 1);
-    return qn1_x(D, i, j);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_fstar(Dev<T> D)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    const int i = (int)blockIdx.x * 32 + (int)threadIdx.x, j = (int)blockIdx.y * 8 + (int)threadIdx.y;
-    const int nx = D.nx, ny = D.ny, pitch = D.pitch;
-    if (i >= nx || j >= ny) return;
-    const long long o = fidx(D, i, j);
-    T q00, q01, q02, q10, q12, q20, q21, q22;  // q[dj][di] at (i + di - 1, j + dj - 1)
-    if (i > 0 && i < nx - 1 && j > 0 && j < ny - 1) {
-        const T *Qp = D.Q + o;
-        q00 = Qp[-pitch - 1]; q01 = Qp[-pitch]; q02 = Qp[-pitch + 1];
-        q10 = Qp[-1]; q12 = Qp[1];
-        q20 = Qp[pitch - 1]; q21 = Qp[pitch]; q22 = Qp[pitch + 1];
-    } else {
-        q00 = qn1_xy(D, i - 1, j - 1); q01 = qn1_xy(D, i, j - 1); q02 = qn1_xy(D, i + 1, j - 1);
-        q10 = qn1_xy(D, i - 1, j); q12 = qn1_xy(D, i + 1, j);
-        q20 = qn1_xy(D, i - 1, j + 1); q21 = qn1_xy(D, i, j + 1); q22 = qn1_xy(D, i + 1, j + 1);
-    }
-    const T *bp = D.bC + o;
-    const T ws = D.w_s;
-    const T d = tmax(ws - bp[0], (T)0);
-    const T ddx = tmax(ws - bp[1], (T)0) - tmax(ws - bp[-1], (T)0);
-    const T ddy = tmax(ws - bp[pitch], (T)0) - tmax(ws - bp[-pitch], (T)0);
-    const T c1 = (T)0.25 * D.rdx * D.rdy / (T)6, c2 = (D.Bd + (T)1 / (T)3) * (T)0.25 * D.rdx * D.rdy;
-    const T dqx = q12 - q10, dqy = q21 - q01, dqxy = (q22 - q02) - (q20 - q00);
-    T f = d * (c1 * (ddx * dqy + ddy * dqx) + c2 * d * dqxy);
-    if (i == 0) f += D.corrW[j];
-    if (i == nx - 1) f += D.corrE[j];
-    D.dU[o] += f;
-}
-
-// ---- one warp per x-line, right-hand side complete in dU
-//
-// Follows k_fstar (dU already holds F*(Q^{n+1}) and the maker corrections).
-// Warp w of block b solves row j = b * XW_WARPS + w in chunks of 32 K
-// elements (lane l owns the K contiguous elements l K ... of a chunk); the
-// forward sweep keeps y in the warp's shared-memory row.  Each lane loads the
-// next chunk's inputs while it works on the current one: dU, m, e in the
-// forward sweep, c', P, cP, w in the back substitution (Q, bC and the sponge
-// profile, read after the scan, are issued at the top of the chunk).  The
-// ragged end of the row is handled in the last chunk only.  Same arithmetic
-// as k_xsolve.
-template <typename T, int K>
-__global__ void __launch_bounds__(32 * XW_WARPS, 4) k_xsolve_wl(Dev<T> D, int yrow, double forced_dt_next)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double smax[XW_WARPS];
-    constexpr int SP = 32 * K;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *ys = reinterpret_cast<T *>(smem_raw) + (size_t)wid * yrow;
-    const int j = (int)blockIdx.x * XW_WARPS + wid;
-    const int nx = D.nx, ny = D.ny;
-    const int nch = (nx + SP - 1) / SP;
-    T rate = (T)0, poison = (T)0;
-    if (j < ny) {
-        const long long rowo = fidx(D, 0, j);
-        const int ibl = lane * K;
-        T nr[K], nm[K], ne[K];
-        vload_k<T, K>(D.dU + rowo + ibl, nr);
-        vload_k<T, K>(D.fxm + rowo + ibl, nm);
-        vload_k<T, K>(D.fxe + rowo + ibl, ne);
-        T carry = (T)0;
-        for (int c = 0; c < nch; c++) {
-            T r[K], m[K], e[K];
-#pragma unroll
-            for (int q = 0; q < K; q++) { r[q] = nr[q]; m[q] = nm[q]; e[q] = ne[q]; }
-            if (c + 1 < nch) {
-                const long long o = rowo + (c + 1) * SP + ibl;
-                vload_k<T, K>(D.dU + o, nr);
-                vload_k<T, K>(D.fxm + o, nm);
-                vload_k<T, K>(D.fxe + o, ne);
-            }
-            const int ib = c * SP + ibl;
-            if (c == nch - 1) {
-#pragma unroll
-                for (int q = 0; q < K; q++)
-                    if (ib + q >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
-            }
-            T A = (T)1, B = (T)0;
-#pragma unroll
-            for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                T Ap = __shfl_up_sync(0xffffffffu, A, o);
-                T Bp = __shfl_up_sync(0xffffffffu, B, o);
-                if (lane >= o) { B = A * Bp + B; A = A * Ap; }
-            }
-            T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-            if (lane == 0) { Ae = (T)1; Be = (T)0; }
-            T y = Ae * carry + Be;
-#pragma unroll
-            for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = y; }
-            vstore_k<T, K>(ys + ib, r);
-            carry = __shfl_sync(0xffffffffu, y, 31);
-        }
-        __syncwarp();
-        // back substitution, last chunk first
-        const T gyj = D.gy[j], ws = D.w_s;
-        T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo;
-        T *wrow = D.w[cf.wc ^ 1] + rowo;
-        T nc[K], nP[K], ncP[K], nw[K];
-        {
-            const int ib = (nch - 1) * SP + ibl;
-            vload_k<T, K>(D.fxc + rowo + ib, nc);
-            vload_k<T, K>(Pr + ib, nP);
-            if (D.kahan) vload_k<T, K>(cPr + ib, ncP);
-            vload_k<T, K>(wrow + ib, nw);
-        }
-        carry = (T)0;
-        for (int c = nch - 1; c >= 0; c--) {
-            const int ib = c * SP + ibl;
-            T cc[K], Pv[K], cPv[K], wv[K], Qv[K], bv[K], gxv[K], x[K];
-#pragma unroll
-            for (int q = 0; q < K; q++) { cc[q] = nc[q]; Pv[q] = nP[q]; cPv[q] = ncP[q]; wv[q] = nw[q]; }
-            vload_k<T, K>(D.Q + rowo + ib, Qv);
-            vload_k<T, K>(D.bC + rowo + ib, bv);
-            vload_k<T, K>(D.gx + ib, gxv);
-            if (c > 0) {
-                const int ibn = ib - SP;
-                vload_k<T, K>(D.fxc + rowo + ibn, nc);
-                vload_k<T, K>(Pr + ibn, nP);
-                if (D.kahan) vload_k<T, K>(cPr + ibn, ncP);
-                vload_k<T, K>(wrow + ibn, nw);
-            }
-            vload_k<T, K>(ys + ib, x);
-            const bool last = c == nch - 1;
-            if (last) {
-#pragma unroll
-                for (int q = 0; q < K; q++)
-                    if (ib + q >= nx) { cc[q] = (T)0; x[q] = (T)0; }
-            }
-            T al = (T)0, be = (T)1;
-#pragma unroll
-            for (int q = K - 1; q >= 0; q--) { al = x[q] - cc[q] * al; be = -cc[q] * be; }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                T ap = __shfl_down_sync(0xffffffffu, al, o);
-                T bp = __shfl_down_sync(0xffffffffu, be, o);
-                if (lane + o < 32) { al = al + be * ap; be = be * bp; }
-            }
-            T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
-            if (lane == 31) { an = (T)0; bn = (T)1; }
-            T xx = an + bn * carry;
-#pragma unroll
-            for (int q = K - 1; q >= 0; q--) { xx = x[q] - cc[q] * xx; x[q] = xx; }
-            carry = __shfl_sync(0xffffffffu, xx, 0);
-#pragma unroll
-            for (int q = 0; q < K; q++) {
-                const int i = ib + q;
-                if (last && i >= nx) continue;
-                T Pn, cn = (T)0;
-                if (D.kahan) {
-                    T yy = x[q] - cPv[q];
-                    Pn = Pv[q] + yy;
-                    cn = (Pn - Pv[q]) - yy;
-                } else {
-                    Pn = Pv[q] + x[q];
-                }
-                T wq = wv[q];
-                T gm = gxv[q] * gyj;
-                if (gm < (T)1) {
-                    T h = tmax(wq - bv[q], (T)0), d = tmax(ws - bv[q], (T)0);
-                    wq = bv[q] + (d + gm * (h - d));
-                    wrow[i] = wq;
-                    if (D.kahan) cwr[i] = (T)0;
-                    Pn *= gm;
-                    cn *= gm;
-                }
-                Pv[q] = Pn;
-                cPv[q] = cn;
-                T h = tmax(wq - bv[q], (T)0);
-                T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-                T u = iv * Pn, v = iv * Qv[q];
-                T cs = tsqrt(D.g * h);
-                rate = tmax(rate, tmax((fabs(u) + cs) * D.rdx, (fabs(v) + cs) * D.rdy));
-                poison += (wq + Pn) + Qv[q];  // non-finite if any of them is
-            }
-            if (ib < nx) {
-                vstore_k<T, K>(Pr + ib, Pv);
-                if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
-            }
-        }
-    }
-    double rr = (double)rate;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
-    const bool anybad = __any_sync(0xffffffffu, !isfinite(poison));
-    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double mx = 0.0;
-        bool fl = false;
-        for (int q = 0; q < XW_WARPS; q++) {
-            if (smax[q] < 0.0) fl = true;
-            else mx = fmax(mx, smax[q]);
-        }
-        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
-        atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, forced_dt_next, gridDim.x);
-    }
-}
-
 // ------------------------------------------------------------------ utilities
 
 // Eq. 22 rate of the current state (used at creation and after a restore).
@@ -3519,12 +3288,6 @@ cudaError_t configure(int nx)
         e = cudaFuncSetAttribute(k_xsolve_warp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_warp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e == cudaSuccess) {
-        if constexpr (sizeof(T) == 4)
-            e = cudaFuncSetAttribute(k_xsolve_wl<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        else
-            e = cudaFuncSetAttribute(k_xsolve_wl<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    }
     return e;
 }
 
@@ -3532,26 +3295,11 @@ cudaError_t configure(int nx)
 static bool launch_rhs2(const Dev<float> &D, cudaStream_t st, int rows, int ky)
 {
     const int nstrip = (D.nx + SW2_COLS - 1) / SW2_COLS;
-    const bool mb3 = (D.tune_rhs2 & 1) != 0;
-    if (mb3 && D.tune_rows == 0) {
-        // bands sized so that the warps fill one wave of 3 blocks per multiprocessor
-        const long long slots = 4LL * 3 * D.nsm;
-        const long long nband = std::max(1LL, slots / nstrip);
-        // a multiple of the y-chunk rows: a chunk's summary never spans two bands
-        const int q = ky > 0 ? ky : 8;
-        rows = std::max(q, (int)((D.ny + nband - 1) / nband + q - 1) / q * q);
-    }
     const int nband = (D.ny + rows - 1) / rows;
     const int blocks = (int)(((long long)nstrip * nband + 3) / 4);
-    if (mb3) {
-        if (ky == 16) k_rhs_sw2<16, 3><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-        else if (ky == 8) k_rhs_sw2<8, 3><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-        else k_rhs_sw2<0, 3><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-    } else {
-        if (ky == 16) k_rhs_sw2<16, 2><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-        else if (ky == 8) k_rhs_sw2<8, 2><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-        else k_rhs_sw2<0, 2><<<blocks, 128, 0, st>>>(D, nstrip, rows);
-    }
+    if (ky == 16) k_rhs_sw2<16><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+    else if (ky == 8) k_rhs_sw2<8><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+    else k_rhs_sw2<0><<<blocks, 128, 0, st>>>(D, nstrip, rows);
     return true;
 }
 static bool launch_rhs2(const Dev<double> &, cudaStream_t, int, int) { return false; }
@@ -3598,15 +3346,6 @@ static bool rhs_fuses_ysum(const Dev<T> &D)
 {
     const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
     return D.tune_rhs != 1 && rhs_fast(D) && D.ysplit && rows != 16 && D.tune_ysum == 0;
-}
-
-// F* by its own pass and the light warp-per-row x-solver: sequential cross
-// form, K = 8 (single) / 4 (double) and the y row fits the shared memory
-template <typename T>
-static bool xsolver_light(const Dev<T> &D, int nx)
-{
-    constexpr int K = sizeof(T) == 4 ? 8 : 4;
-    return D.tune_xws != 0 && D.cross_mode != 0 && xwarp_smem<T, K>(nx) <= 96 * 1024;
 }
 
 // One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
@@ -3690,24 +3429,16 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
-    const bool xws = xsolver_light(D, nx);
-    const bool xwarp = !xws && xsolver_warp(D, nx);
-    const bool grp = !xws && !xwarp && xsolver_grouped(D, nx);
+    const bool xwarp = xsolver_warp(D, nx);
+    const bool grp = !xwarp && xsolver_grouped(D, nx);
     const bool pipe = !grp && xsolver_staging_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM;
-    const bool tma = xws || xwarp || grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
+    const bool tma = xwarp || grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
     if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (xws) {
-        k_fstar<T><<<dim3((nx + 31) / 32, (ny + 7) / 8), dim3(32, 8), 0, st>>>(D);
-        if (ev) cudaEventRecord(ev[4], st);
-        const int xb = (ny + XW_WARPS - 1) / XW_WARPS;
-        constexpr int K = sizeof(T) == 4 ? 8 : 4;
-        const int yrow = (nx + 32 * K - 1) / (32 * K) * (32 * K);
-        k_xsolve_wl<T, K><<<xb, 32 * XW_WARPS, xwarp_smem<T, K>(nx), st>>>(D, yrow, forced_dt_next);
-    } else if (xwarp) {
+    if (xwarp) {
         const int xb = (ny + XW_WARPS - 1) / XW_WARPS;
         if (K == 4) {
             const int yrow = (nx + 127) / 128 * 128;
@@ -3747,7 +3478,7 @@ int xsolver_staged(const Dev<T> &D, int nx)
     const int K = x_chunk<T>(nx, D.tune_xk);
     const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const size_t xs = xtma_smem<T>(thr * K, D.hx);
-    return xsolver_light(D, nx) || xsolver_warp(D, nx) || xsolver_grouped(D, nx) ||
+    return xsolver_warp(D, nx) || xsolver_grouped(D, nx) ||
            (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
 }
 
@@ -3756,10 +3487,9 @@ template <typename T>
 int step_launches(const Dev<T> &D)
 {
     const int nx = D.nx;
-    const bool light = xsolver_light(D, nx);
-    const bool ghost_q = D.cross_mode != 0 && !xsolver_staged(D, nx) && !light;
+    const bool ghost_q = D.cross_mode != 0 && !xsolver_staged(D, nx);
     const int ylaunch = D.ysplit ? (rhs_fuses_ysum(D) ? 2 : 3) : 1;
-    return 1 /* ghost */ + 1 /* rhs */ + ylaunch + (ghost_q ? 1 : 0) + (light ? 1 : 0) /* F* */ + 1 /* x-solver */;
+    return 1 /* ghost */ + 1 /* rhs */ + ylaunch + (ghost_q ? 1 : 0) + 1 /* x-solver */;
 }
 
 template <typename T>

@@ -232,8 +232,7 @@ def test_bounded_wait_times_out():
 @pytest.mark.parametrize("tune", [(0, 0, 1, 0), (0, 0, 2, 0), (0, 0, 3, 0), (8, 256, 0, 16), (32, 512, 0, 64),
                                   (0, 0, 8, 0, 4), (0, 0, 8, 0, 8), (0, 0, 0, 0, 4),
                                   (0, 0, 16, 0, 4), (0, 0, 16, 0, 8), (0, 0, 0, 0, 0, 0, 1), (0, 0, 0, 32, 0, 16),
-                                  (0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 32, 0, 0, 3), (0, 0, 0, 0, 0, 0, 0, 1),
-                                  (0, 0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 0, 4, 0, 0, 2)])
+                                  (0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 32, 0, 0, 3), (0, 0, 4, 0, 4), (0, 0, 4, 0, 8)])
 def test_kernel_variants_match_oracle(tune):
     # every kernel shape (tiled or sliding-window RHS, TMA-staged or register
     # x-solver, y-solver chunk sizes) gives the same step to FP64 round-off
@@ -247,31 +246,3 @@ def test_kernel_variants_match_oracle(tune):
     with bsq.Domain(case, precision="fp32", tune=tune) as d:
         d.step_dt(dts)
         assert rel(d.read("eta"), o.get("eta")) <= FP32_TOL, tune
-
-
-@pytest.mark.parametrize("name", ["ragged_multi_segment", "planar_beach_jonswap", "tall_multi_chunk", "hump_2d_walls",
-                                  "long_rows"])
-def test_staged_warp_xsolver_matches_oracle(name):
-    # the warp-per-row x-solver with bulk-copied chunks, on rows of one to
-    # three chunks (first, interior and last chunk) with ragged tails, wave
-    # makers and walls
-    tune = (0, 0, 0, 0, 0, 0, 0, 2)
-    case = _hump_case(700, 24, dx=0.05, seed=9) if name == "long_rows" else CASES[name]()
-    o = _oracle(case)
-    dts = o.run(60)
-    with bsq.Domain(case, precision="fp64", tune=tune) as d:
-        d.step_dt(dts)
-        for f in ("eta", "P", "Q"):
-            ref = o.get(f)
-            if np.linalg.norm(ref) == 0.0:
-                assert np.abs(d.read(f)).max() <= 1e-13, (name, f)
-            else:
-                assert rel(d.read(f), ref) <= FP64_TOL, (name, f)
-    with bsq.Domain(case, precision="fp32", tune=tune) as d:
-        d.step_dt(dts)
-        ref = o.get("eta")
-        got = d.read("eta")
-        if np.sqrt(np.mean(ref ** 2)) > 1e-4:
-            assert rel(got, ref) <= FP32_TOL, name
-        else:
-            assert np.abs(got - ref).max() <= 2e-6, name
