@@ -261,20 +261,22 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
             fxc[cidx(i, j)] = (T)cprev;
         }
     }
-    for (int i = 0; i < nx; i++) {
-        double cprev = 0.0;
-        for (int j = 0; j < ny; j++) {
+    // y-lines: every column's recurrence advances one row at a time, so the
+    // fields are walked in memory order
+    std::vector<double> cprevy((size_t)nx, 0.0);
+    for (int j = 0; j < ny; j++) {
+        for (int i = 0; i < nx; i++) {
             double A, B, C;
             coefy(i, j, A, B, C);
             if (j == 0) { cS[i] = A; if (bt[BSQ_SOUTH] != BSQ_BC_MAKER) B -= A; A = 0.0; }
             if (j == ny - 1) { cN[i] = C; if (bt[BSQ_NORTH] != BSQ_BC_MAKER) B -= C; C = 0.0; }
             if (!(fabs(B) > fabs(A) + fabs(C))) return BSQ_ERR_ARG;
-            double den = B - A * cprev;
+            double den = B - A * cprevy[i];
             double m = 1.0 / den;
-            cprev = C * m;
+            cprevy[i] = C * m;
             fym[cidx(i, j)] = (T)m;
             fye[cidx(i, j)] = (T)(-A * m);
-            fyc[cidx(i, j)] = (T)cprev;
+            fyc[cidx(i, j)] = (T)cprevy[i];
         }
     }
     // sponge profiles: gamma(r) = 1/2 + 1/2 cos(pi (1 - r/L)) inside a band of
@@ -667,6 +669,8 @@ struct bsq_batch {
     double *d_tend, *h_tend;
     Ctl *d_ctl, *h_ctl;  // gathered controller states (h_ctl pinned)
     BatchPlan plan;
+    std::vector<RhsGroup> rhs_grp;          // descriptors of each RHS launch (single precision)
+    std::vector<int> rhs_grp_nb, rhs_grp_off;
     cudaGraphExec_t graph;
     int graph_steps;
     double timeout_s;
@@ -699,6 +703,8 @@ static void batch_free(bsq_batch *b)
     delete b;
 }
 
+template <typename T> static constexpr bool pair_rhs() { return sizeof(T) == 4; }
+
 // The block tables of every stage for the member domains with the given tile
 // shapes (RHS rows per warp, x elements per lane, y rows per chunk); with the
 // defaults each domain's blocks are laid out exactly as its own single-domain
@@ -722,18 +728,33 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     std::vector<Dev<T>> hD(n);
     for (int d = 0; d < n; d++) {
         const Dev<T> &D = dev_of<T>(b->doms[d]);
-        hD[d] = D;
-        const int nx = D.nx, ny = D.ny;
         if (!D.ysplit || D.tune_yk != 0 || D.tune_xk != 0) return BSQ_ERR_ARG;
         fast = fast && D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 &&
                (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
         theta1 = theta1 && D.theta == (T)1;
+    }
+    // the single-precision fast RHS pairs two columns per lane (strips of 60),
+    // the others hold one column per lane (strips of 28)
+    const bool pair = fast && pair_rhs<T>() && rows != 16;
+    b->rhs_grp.clear();
+    b->rhs_grp_nb.clear();
+    b->rhs_grp_off.clear();
+    for (int d = 0; d < n; d++) {
+        const Dev<T> &D = dev_of<T>(b->doms[d]);
+        hD[d] = D;
+        const int nx = D.nx, ny = D.ny;
         const long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
         const int gb = (int)((nwork + 255) / 256);
         for (int q = 0; q < gb; q++) tg.push_back(make_int4(d, q, gb, 0));
-        const int nstrip = (nx + 27) / 28, nband = (ny + rows - 1) / rows;
+        const int nstrip = pair ? (nx + 59) / 60 : (nx + 27) / 28, nband = (ny + rows - 1) / rows;
         const int rb = (int)(((long long)nstrip * nband + 3) / 4);
-        for (int q = 0; q < rb; q++) tr.push_back(make_int4(d, q, nstrip, 0));
+        // paired kernel: domains in groups of RHS_GROUP, one launch per group
+        if (pair && d % RHS_GROUP == 0) {
+            b->rhs_grp_off.push_back((int)tr.size());
+            b->rhs_grp_nb.push_back(0);
+        }
+        for (int q = 0; q < rb; q++) tr.push_back(make_int4(pair ? d % RHS_GROUP : d, q, nstrip, rows));
+        if (pair) b->rhs_grp_nb.back() += rb;
         const int nch = (ny + KY - 1) / KY;
         const int gx = (nx + 31) / 32, gy = (nch + 7) / 8;
         for (int by = 0; by < gy; by++)
@@ -772,6 +793,19 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     P.t_ysum = (const int4 *)(base + o_s); P.t_yscan = (const int4 *)(base + o_c);
     P.t_x = (const int4 *)(base + o_x);
     P.rhs_fast = fast ? 1 : 0;
+    P.rhs_pair = pair ? 1 : 0;
+    P.rhs_ngroups = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (pair) {
+            const int ng = (n + RHS_GROUP - 1) / RHS_GROUP;
+            b->rhs_grp.assign(ng, RhsGroup{});
+            for (int d = 0; d < n; d++) b->rhs_grp[d / RHS_GROUP].d[d % RHS_GROUP] = hD[d];
+            P.rhs_ngroups = ng;
+        }
+    }
+    P.rhs_grp = b->rhs_grp.data();
+    P.rhs_grp_nb = b->rhs_grp_nb.data();
+    P.rhs_grp_off = b->rhs_grp_off.data();
     P.rhs_theta1 = theta1 ? 1 : 0;
     P.yrow_max = yrow_max;
     P.rhs_rows = rows;
@@ -924,7 +958,13 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
 
 extern "C" int bsq_batch_size(const bsq_batch *b) { return b ? (int)b->doms.size() : 0; }
 
-extern "C" int bsq_batch_launches_per_step(const bsq_batch *b) { return b ? 6 : 0; }
+extern "C" int bsq_batch_launches_per_step(const bsq_batch *b)
+{
+    if (!b) return 0;
+    // the fast RHS forms the y-line chunk summaries itself; the paired RHS is one
+    // launch per group of RHS_GROUP domains
+    return (b->plan.rhs_fast ? 5 : 6) + (b->plan.rhs_pair ? b->plan.rhs_ngroups - 1 : 0);
+}
 
 // Try every tile-shape combination on the batch itself (real steps), keep the
 // fastest.

@@ -89,6 +89,15 @@ struct Dev {
     Coef *coef;
 };
 
+// Descriptors of up to RHS_GROUP member domains passed by value to one
+// launch of the batched single-precision RHS kernel: kernel parameters live
+// in the constant bank, which the kernel reads like the single-domain kernel
+// reads its own descriptor (a copy in shared memory costs it registers).
+constexpr int RHS_GROUP = 48;
+struct RhsGroup {
+    Dev<float> d[RHS_GROUP];
+};
+
 // Block tables of a batched step: entry b of a stage's table says which
 // domain block b of that stage's single launch works on, and where (the
 // meaning of the remaining fields is the stage's, see the batched kernels).
@@ -97,6 +106,10 @@ struct BatchPlan {
     int nb_ghost, nb_rhs, nb_ysum, nb_yscan, nb_x;  // blocks of each stage's launch
     const int4 *t_ghost, *t_rhs, *t_ysum, *t_yscan, *t_x;
     int rhs_fast, rhs_theta1;                     // RHS variant shared by all domains
+    int rhs_pair;                                 // single precision: two columns per lane (k_rhs_sw2 body)
+    int rhs_ngroups;                              // with rhs_pair: launches of the RHS stage, and per
+    const RhsGroup *rhs_grp;                      // launch (host arrays) its descriptors, blocks and
+    const int *rhs_grp_nb, *rhs_grp_off;          // first entry in t_rhs
     int yrow_max;                                 // x-solver shared row length (elements)
     int rhs_rows, xk, ky;                         // tile shapes: RHS rows per warp, x elements per
                                                   // lane, y rows per chunk (the autotuner's knobs)

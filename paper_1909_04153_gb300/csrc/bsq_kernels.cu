@@ -1168,17 +1168,20 @@ __device__ __forceinline__ void recon_pair(f2 m, f2 z, f2 p, f2 &lo, f2 &hi)
     lo = fma2(sc2(-0.5f), s, z);
     hi = fma2(sc2(0.5f), s, z);
 }
-// water level with the positivity fix against the face beds blo, bhi
+// water level with the positivity fix against the face beds blo, bhi.  The
+// cell mean is not below the mean of its two face beds (the update clamps
+// w >= b at the centre, which is that mean), so at most one face value lies
+// below its bed: the face below its bed is raised to it and the other face
+// takes the difference, keeping the sum of the two (2 w): with
+//   delta = max(bhi - hi, 0) - max(blo - lo, 0),
+// hi += delta and lo -= delta, branch free.
 __device__ __forceinline__ void recon_w_pair(f2 m, f2 z, f2 p, f2 blo, f2 bhi, f2 &lo, f2 &hi)
 {
     const f2 s = slope2(m, z, p);
     const f2 a = fma2(sc2(0.5f), s, z), b = fma2(sc2(-0.5f), s, z);
-    const f2 za = mul2(sc2(2.0f), z);
-    const f2 ra = sub2(za, bhi), rb = sub2(za, blo);
-    const bool hx = a.x < bhi.x, lx = !hx && b.x < blo.x;
-    const bool hy = a.y < bhi.y, ly = !hy && b.y < blo.y;
-    hi = mk2(hx ? bhi.x : (lx ? rb.x : a.x), hy ? bhi.y : (ly ? rb.y : a.y));
-    lo = mk2(hx ? ra.x : (lx ? blo.x : b.x), hy ? ra.y : (ly ? blo.y : b.y));
+    const f2 delta = sub2(max2(sub2(bhi, a), sc2(0.0f)), max2(sub2(blo, b), sc2(0.0f)));
+    hi = add2(a, delta);
+    lo = sub2(b, delta);
 }
 
 struct FS2 {
@@ -1204,9 +1207,10 @@ __device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f
     const f2 unL = DIR == 0 ? L.u : L.v, unR = DIR == 0 ? R.u : R.v;
     const f2 ap = max2(max2(add2(unL, L.c), add2(unR, R.c)), sc2(0.0f));
     const f2 am = min2(min2(sub2(unL, L.c), sub2(unR, R.c)), sc2(0.0f));
-    const f2 den = sub2(ap, am);
-    const bool mvx = den.x > 0.0f, mvy = den.y > 0.0f;
-    const f2 inv = mk2(trcp(mvx ? den.x : 1.0f), trcp(mvy ? den.y : 1.0f));
+    // a+ = a- = 0 (both sides dry): with den floored at 1e-30 every term below
+    // is an exact zero, which is the flux of Eq. 5 in that case
+    const f2 den = max2(sub2(ap, am), sc2(1e-30f));
+    const f2 inv = mk2(trcp(den.x), trcp(den.y));
     const f2 pL = mul2(L.h, L.u), qL = mul2(L.h, L.v), pR = mul2(R.h, R.u), qR = mul2(R.h, R.v);
     const f2 hg = sc2(0.5f * g);
     const f2 hhL = mul2(mul2(hg, L.h), L.h), hhR = mul2(mul2(hg, R.h), R.h);
@@ -1223,9 +1227,9 @@ __device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f
     const f2 t0 = fma2(k, sub2(R.h, L.h), mul2(fma2(nam, FR0, mul2(ap, FL0)), inv));
     const f2 t1 = fma2(k, sub2(pR, pL), mul2(fma2(nam, FR1, mul2(ap, FL1)), inv));
     const f2 t2 = fma2(k, sub2(qR, qL), mul2(fma2(nam, FR2, mul2(ap, FL2)), inv));
-    H0 = mk2(mvx ? t0.x : 0.0f, mvy ? t0.y : 0.0f);
-    H1 = mk2(mvx ? t1.x : 0.0f, mvy ? t1.y : 0.0f);
-    H2 = mk2(mvx ? t2.x : 0.0f, mvy ? t2.y : 0.0f);
+    H0 = t0;
+    H1 = t1;
+    H2 = t2;
 }
 
 constexpr int SW2_COLS = 60;  // interior columns per warp strip (two per lane, lanes 1..30)
@@ -1743,7 +1747,7 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
-    const int i = bx * 32 + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     const int k = by * blockDim.y + threadIdx.y;
     const int nx = D.nx, ny = D.ny;
     if (i >= nx || k >= nch) return;
@@ -3413,8 +3417,11 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
             else k_ysum<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.ysums);
         }
         k_yscan<T><<<(int)(((long long)nx * 32 + 255) / 256), 256, 0, st>>>(D, nch, D.ysums, D.yin, D.yxa);
-        if (KY == 8) k_yapply<T, 8><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
-        else k_yapply<T, 16><<<gb2, dim3(32, 8), 0, st>>>(D, nch, D.yin, D.yxa);
+        // one chunk of 256 adjacent columns per block: each row segment a block
+        // reads is 1 KB contiguous
+        const dim3 gw((nx + 255) / 256, nch);
+        if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
     } else {
         int CW, NCH, kch;
         ysolve_shape<T>(D, CW, NCH, kch);
@@ -3660,9 +3667,28 @@ cudaError_t configure_batch(int yrow_max)
     return e;
 }
 
+// table entry: (domain within the group, block of that domain, strips of 60
+// columns, rows per warp); the group's descriptors are a kernel parameter
+template <int YS>
+__global__ void __launch_bounds__(128, 2) k_rhs_sw2_g(const __grid_constant__ RhsGroup G, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    rhs_sw2_body<YS>(G.d[e.x], e.y, e.z, e.w);
+}
+
 template <typename T, int ROWS>
 static void launch_batch_rhs(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (P.rhs_pair) {
+            for (int g = 0; g < P.rhs_ngroups; g++) {
+                const int4 *tab = P.t_rhs + P.rhs_grp_off[g];
+                if (P.ky == 16) k_rhs_sw2_g<16><<<P.rhs_grp_nb[g], 128, 0, st>>>(P.rhs_grp[g], tab);
+                else k_rhs_sw2_g<8><<<P.rhs_grp_nb[g], 128, 0, st>>>(P.rhs_grp[g], tab);
+            }
+            return;
+        }
+    }
     if (P.rhs_fast && P.ky == 16) k_rhs_sw_b<T, ROWS, true, true, 16><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
     else if (P.rhs_fast) k_rhs_sw_b<T, ROWS, true, true, 8><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);
     else if (P.rhs_theta1) k_rhs_sw_b<T, ROWS, true, false><<<P.nb_rhs, 128, 0, st>>>(Ds, P.t_rhs);

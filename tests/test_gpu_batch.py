@@ -178,3 +178,27 @@ def test_autotune_fp32_picks_a_shape():
         assert list(b.advance(max_steps=8)) == [8, 8, 8]
     for d in doms:
         d.close()
+
+
+def test_batch_larger_than_one_rhs_group():
+    # the single-precision RHS stage launches once per group of 48 members
+    # (their descriptors are a kernel parameter); members of the first and of
+    # the second group equal their batch-of-one results bitwise
+    rng = np.random.default_rng(5)
+    sides = [int(32 * rng.integers(1, 4)) for _ in range(53)]
+    cases = [W.random_basin(n, seed=100 + k, forcing="solitary" if k % 2 else "jonswap")
+             for k, n in enumerate(sides)]
+    steps = 24
+    doms = [bsq.Domain(c, precision="fp32", graph_steps=8) for c in cases]
+    with bsq.Batch(doms) as b:
+        done = b.advance(max_steps=steps)
+    assert list(done) == [steps] * len(cases)
+    for k in (0, 1, 47, 48, 52):
+        s, n = _alone(cases[k], "fp32", max_steps=steps)
+        assert n == steps
+        assert doms[k].info()["t"] == s.info()["t"]
+        for f in ("eta", "P", "Q"):
+            np.testing.assert_array_equal(doms[k].read(f), s.read(f))
+        s.close()
+    for d in doms:
+        d.close()
