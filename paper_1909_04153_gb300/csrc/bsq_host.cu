@@ -202,83 +202,23 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     const bool kahan = p.kahan && sizeof(T) == 4;
     dm->p.kahan = kahan ? 1 : 0;
 
-    // ---- static geometry in FP64 on the host
-    const int cx = nx + 5, cy = ny + 5;
-    std::vector<double> corner((size_t)cx * cy);
-    for (int j = -2; j <= ny + 2; j++) {
-        int js = j < 0 ? -j : (j > ny ? 2 * ny - j : j);
-        for (int i = -2; i <= nx + 2; i++) {
-            int is = i < 0 ? -i : (i > nx ? 2 * nx - i : i);
-            corner[(size_t)(j + 2) * cx + (i + 2)] = bed[(size_t)is + (size_t)js * (nx + 1)];
-        }
-    }
-    auto K = [&](int i, int j) { return corner[(size_t)(j + 2) * cx + (i + 2)]; };
-    auto cidx = [&](int i, int j) { return (size_t)(j + 2) * pitch + (i + hx); };
-    std::vector<double> bC((size_t)fs, 0.0), dd((size_t)fs, 0.0);
-    for (int j = -2; j <= ny + 1; j++)
-        for (int i = -2; i <= nx + 1; i++) {
-            double bw = 0.5 * (K(i, j) + K(i, j + 1)), be = 0.5 * (K(i + 1, j) + K(i + 1, j + 1));
-            double bs = 0.5 * (K(i, j) + K(i + 1, j)), bn = 0.5 * (K(i, j + 1) + K(i + 1, j + 1));
-            double b = 0.25 * (bw + be + bs + bn);
-            bC[cidx(i, j)] = b;
-            dd[cidx(i, j)] = fmax(p.w_s - b, 0.0);
-        }
-    auto D_ = [&](int i, int j) { return dd[cidx(i, j)]; };
-    const double kB = p.Bd + 1.0 / 3.0;
-    // Eq. 21 coefficients of one cell, x and y
-    auto coefx = [&](int i, int j, double &A, double &B, double &C) {
-        double d = D_(i, j), gx = (D_(i + 1, j) - D_(i - 1, j)) / (2.0 * p.dx);
-        A = d * gx / (6.0 * p.dx) - kB * d * d / (p.dx * p.dx);
-        B = 1.0 + 2.0 * kB * d * d / (p.dx * p.dx);
-        C = -d * gx / (6.0 * p.dx) - kB * d * d / (p.dx * p.dx);
-    };
-    auto coefy = [&](int i, int j, double &A, double &B, double &C) {
-        double d = D_(i, j), gy = (D_(i, j + 1) - D_(i, j - 1)) / (2.0 * p.dy);
-        A = d * gy / (6.0 * p.dy) - kB * d * d / (p.dy * p.dy);
-        B = 1.0 + 2.0 * kB * d * d / (p.dy * p.dy);
-        C = -d * gy / (6.0 * p.dy) - kB * d * d / (p.dy * p.dy);
-    };
+    // ---- static geometry, line factors and initial state are computed on the
+    // device (launch_setup); the host keeps the per-side and per-line vectors
+    const int cx = nx + 5;
     const int *bt = dm->bnd.type;
-    // Thomas factors per line with the boundary rows closed: wall/sponge =
-    // odd mirror of the normal flux (diagonal minus the outside coefficient),
-    // maker = outside value known (moved to the right-hand side each step).
-    std::vector<T> fxm((size_t)fs, (T)0), fxe((size_t)fs, (T)1), fxc((size_t)fs, (T)0);
-    std::vector<T> fym((size_t)fs, (T)0), fye((size_t)fs, (T)1), fyc((size_t)fs, (T)0);
-    std::vector<double> cW(ny), cE(ny), cS(nx), cN(nx);
-    for (int j = 0; j < ny; j++) {
-        double cprev = 0.0;
-        for (int i = 0; i < nx; i++) {
-            double A, B, C;
-            coefx(i, j, A, B, C);
-            if (i == 0) { cW[j] = A; if (bt[BSQ_WEST] != BSQ_BC_MAKER) B -= A; A = 0.0; }
-            if (i == nx - 1) { cE[j] = C; if (bt[BSQ_EAST] != BSQ_BC_MAKER) B -= C; C = 0.0; }
-            if (!(fabs(B) > fabs(A) + fabs(C))) return BSQ_ERR_ARG;
-            double den = B - A * cprev;
-            double m = 1.0 / den;
-            cprev = C * m;
-            fxm[cidx(i, j)] = (T)m;
-            fxe[cidx(i, j)] = (T)(-A * m);
-            fxc[cidx(i, j)] = (T)cprev;
-        }
-    }
-    // y-lines: every column's recurrence advances one row at a time, so the
-    // fields are walked in memory order
-    std::vector<double> cprevy((size_t)nx, 0.0);
-    for (int j = 0; j < ny; j++) {
-        for (int i = 0; i < nx; i++) {
-            double A, B, C;
-            coefy(i, j, A, B, C);
-            if (j == 0) { cS[i] = A; if (bt[BSQ_SOUTH] != BSQ_BC_MAKER) B -= A; A = 0.0; }
-            if (j == ny - 1) { cN[i] = C; if (bt[BSQ_NORTH] != BSQ_BC_MAKER) B -= C; C = 0.0; }
-            if (!(fabs(B) > fabs(A) + fabs(C))) return BSQ_ERR_ARG;
-            double den = B - A * cprevy[i];
-            double m = 1.0 / den;
-            cprevy[i] = C * m;
-            fym[cidx(i, j)] = (T)m;
-            fye[cidx(i, j)] = (T)(-A * m);
-            fyc[cidx(i, j)] = (T)cprevy[i];
-        }
-    }
+    for (int s = 0; s < 4; s++)
+        if (bt[s] < BSQ_BC_WALL || bt[s] > BSQ_BC_MAKER) return BSQ_ERR_ARG;
+    // still depth at cell (i, j), -1 <= i <= nx, -1 <= j <= ny, from the corner bed
+    auto K = [&](int i, int j) {
+        const int is = i < 0 ? -i : (i > nx ? 2 * nx - i : i);
+        const int js = j < 0 ? -j : (j > ny ? 2 * ny - j : j);
+        return bed[(size_t)is + (size_t)js * (nx + 1)];
+    };
+    auto D_ = [&](int i, int j) {
+        const double bw = 0.5 * (K(i, j) + K(i, j + 1)), be = 0.5 * (K(i + 1, j) + K(i + 1, j + 1));
+        const double bs = 0.5 * (K(i, j) + K(i + 1, j)), bn = 0.5 * (K(i, j + 1) + K(i + 1, j + 1));
+        return fmax(p.w_s - 0.25 * (bw + be + bs + bn), 0.0);
+    };
     // sponge profiles: gamma(r) = 1/2 + 1/2 cos(pi (1 - r/L)) inside a band of
     // width L, r from the outer edge; product over sponge sides
     auto sg = [](double r, double L) {
@@ -326,20 +266,6 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
         comp[5 * nc + k] = c * cos(th);
         comp[6 * nc + k] = c * sin(th);
     }
-    // initial state: h = max(d + eta0, 0), w = b + h
-    std::vector<T> w0((size_t)fs, (T)0), Pv((size_t)fs, (T)0), Qv((size_t)fs, (T)0);
-    for (int j = 0; j < ny; j++)
-        for (int i = 0; i < nx; i++) {
-            size_t c = cidx(i, j), k = (size_t)i + (size_t)j * nx;
-            double h = fmax(dd[c] + (eta0 ? eta0[k] : 0.0), 0.0);
-            w0[c] = (T)(bC[c] + h);
-            Pv[c] = (T)(P0 ? P0[k] : 0.0);
-            Qv[c] = (T)(Q0 ? Q0[k] : 0.0);
-        }
-    std::vector<T> cornerT(corner.size()), bCT((size_t)fs);
-    for (size_t q = 0; q < corner.size(); q++) cornerT[q] = (T)corner[q];
-    for (size_t q = 0; q < (size_t)fs; q++) bCT[q] = (T)bC[q];
-
     // ---- device memory: one allocation
     const Layout L = layout<T>(nx, ny, p.tune[4], kahan, nc);
     const size_t fb = L.fb;
@@ -420,28 +346,51 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.yxa = D.ysums + 6 * nchy;
     dm->n_state_fields = nstate + 15;
 
-    // uploads (synchronous copies from pageable memory, then a stream sync)
-    const size_t fbytes = (size_t)fs * sizeof(T);
+    // device-side set-up from device copies of the caller's arrays: geometry,
+    // Thomas factors (FP64, Eq. 21), initial state
     CK(cudaStreamSynchronize(dm->stream));
-    CK(cudaMemcpy(D.w[0], w0.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.P, Pv.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.Q, Qv.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.bC, bCT.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fxm, fxm.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fxe, fxe.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fxc, fxc.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fym, fym.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fye, fye.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.fyc, fyc.data(), fbytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(D.corner, cornerT.data(), cornerT.size() * sizeof(T), cudaMemcpyHostToDevice));
+    {
+        const size_t nbed = (size_t)(nx + 1) * (ny + 1), ncell = (size_t)nx * ny;
+        const size_t nin = nbed + ncell * ((eta0 ? 1 : 0) + (P0 ? 1 : 0) + (Q0 ? 1 : 0));
+        const size_t nscr = 2 * (size_t)fs;
+        char *tmp = nullptr;
+        const size_t tbytes = (nin + nscr) * sizeof(double) + 256;
+        // stream-ordered scratch: no device-wide synchronisation (other domains may be running)
+        if (cudaMallocAsync((void **)&tmp, tbytes, dm->stream) != cudaSuccess) return BSQ_ERR_OOM;
+        double *dtmp = (double *)tmp;
+        SetupArgs A;
+        memset(&A, 0, sizeof(A));
+        size_t o = 0;
+        auto up = [&](const double *h, size_t n) -> const double * {
+            if (!h) return nullptr;
+            double *dst = dtmp + o;
+            o += n;
+            return cudaMemcpyAsync(dst, h, n * sizeof(double), cudaMemcpyHostToDevice, dm->stream) == cudaSuccess
+                       ? dst
+                       : nullptr;
+        };
+        A.bed = up(bed, nbed);
+        A.eta0 = up(eta0, ncell);
+        A.P0 = up(P0, ncell);
+        A.Q0 = up(Q0, ncell);
+        A.bCd = dtmp + o;
+        A.dd = dtmp + o + fs;
+        A.cW = cb; A.cE = cb + ny; A.cS = cb + 2 * ny; A.cN = cb + 2 * ny + nx;
+        A.bad = (unsigned *)(tmp + (nin + nscr) * sizeof(double));
+        A.w_s = p.w_s; A.Bd = p.Bd; A.dx = p.dx; A.dy = p.dy;
+        for (int s = 0; s < 4; s++) A.bt[s] = bt[s] == BSQ_BC_MAKER ? MAKER : (bt[s] == BSQ_BC_SPONGE ? SPONGE : WALL);
+        unsigned bad = 0;
+        cudaError_t e = cudaMemsetAsync(A.bad, 0, sizeof(unsigned), dm->stream);
+        if (e == cudaSuccess && (!A.bed || (eta0 && !A.eta0) || (P0 && !A.P0) || (Q0 && !A.Q0))) e = cudaErrorUnknown;
+        if (e == cudaSuccess) e = launch_setup<T>(D, dm->stream, A);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, A.bad, sizeof(unsigned), cudaMemcpyDeviceToHost, dm->stream);
+        cudaFreeAsync(tmp, dm->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(dm->stream);
+        if (e != cudaSuccess) return BSQ_ERR_CUDA;
+        if (bad) return BSQ_ERR_ARG;  // a line system is not diagonally dominant
+    }
     CK(cudaMemcpy(D.gx, gx.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.gy, gy.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
-    std::vector<double> cbh;
-    cbh.insert(cbh.end(), cW.begin(), cW.end());
-    cbh.insert(cbh.end(), cE.begin(), cE.end());
-    cbh.insert(cbh.end(), cS.begin(), cS.end());
-    cbh.insert(cbh.end(), cN.begin(), cN.end());
-    CK(cudaMemcpy(cb, cbh.data(), cbh.size() * sizeof(double), cudaMemcpyHostToDevice));
     if (nc > 0) CK(cudaMemcpy(cp, comp.data(), comp.size() * sizeof(double), cudaMemcpyHostToDevice));
     Ctl c0;
     memset(&c0, 0, sizeof(c0));

@@ -89,6 +89,18 @@ struct Dev {
     Coef *coef;
 };
 
+// Inputs of the device-side set-up of a new domain (geometry, line factors,
+// initial state): device copies of the caller's arrays and FP64 scratch.
+struct SetupArgs {
+    const double *bed;               // (nx+1) x (ny+1) corner elevations, row-major
+    const double *eta0, *P0, *Q0;    // nx x ny, or null
+    double *bCd, *dd;                // scratch: bed at centres and still depth, padded fields
+    double *cW, *cE, *cS, *cN;       // boundary coefficients of the line systems (outputs)
+    unsigned *bad;                   // set when a line is not diagonally dominant
+    double w_s, Bd, dx, dy;
+    int bt[4];                       // boundary type per side (W, E, S, N)
+};
+
 // Descriptors of up to RHS_GROUP member domains passed by value to one
 // launch of the batched single-precision RHS kernel: kernel parameters live
 // in the constant bank, which the kernel reads like the single-domain kernel

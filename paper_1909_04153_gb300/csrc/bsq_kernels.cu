@@ -3123,6 +3123,141 @@ static size_t xtma_smem(int span, int hx)
     return ((size_t)XT_ARR_PLAIN * span + (size_t)XT_ARR_HALO * (span + 2 * hx)) * sizeof(T);
 }
 
+// ------------------------------------------------------------------ set-up of a new domain
+//
+// The static geometry, the line factors and the initial state of a domain,
+// computed on the device in FP64 from device copies of the caller's arrays
+// (KP07 corner bed, Sec. 3; Eq. 21 coefficients; h = max(d + eta0, 0)).
+// bed at the (nx+5) x (ny+5) corners -2..nx+2, mirrored past the edges
+template <typename T>
+__global__ void k_setup_corner(Dev<T> D, SetupArgs A)
+{
+    const int cx = D.nx + 5, cy = D.ny + 5;
+    const long long n = (long long)cx * cy;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % cx) - 2, j = (int)(q / cx) - 2;
+        const int is = i < 0 ? -i : (i > D.nx ? 2 * D.nx - i : i);
+        const int js = j < 0 ? -j : (j > D.ny ? 2 * D.ny - j : j);
+        D.corner[q] = (T)A.bed[(size_t)is + (size_t)js * (D.nx + 1)];
+    }
+}
+
+// bed at the centres (mean of the 4 face values) and still depth, cells -2..nx+1 x -2..ny+1
+template <typename T>
+__global__ void k_setup_centres(Dev<T> D, SetupArgs A)
+{
+    const int w = D.nx + 4, h = D.ny + 4;
+    const long long n = (long long)w * h;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % w) - 2, j = (int)(q / w) - 2;
+        auto K = [&](int a, int b) {
+            const int is = a < 0 ? -a : (a > D.nx ? 2 * D.nx - a : a);
+            const int js = b < 0 ? -b : (b > D.ny ? 2 * D.ny - b : b);
+            return A.bed[(size_t)is + (size_t)js * (D.nx + 1)];
+        };
+        const double bw = 0.5 * (K(i, j) + K(i, j + 1)), be = 0.5 * (K(i + 1, j) + K(i + 1, j + 1));
+        const double bs = 0.5 * (K(i, j) + K(i + 1, j)), bn = 0.5 * (K(i, j + 1) + K(i + 1, j + 1));
+        const double b = 0.25 * (bw + be + bs + bn);
+        const long long c = fidx(D, i, j);
+        A.bCd[c] = b;
+        A.dd[c] = fmax(A.w_s - b, 0.0);
+        D.bC[c] = (T)b;
+    }
+}
+
+// Eq. 21 coefficients of cell (i, j) along a line: a (previous), b (diagonal), c (next)
+__device__ __forceinline__ void eq21_coef(double d, double dm, double dp, double h, double kB, double &a, double &b,
+                                          double &c)
+{
+    const double gd = (dp - dm) / (2.0 * h);
+    a = d * gd / (6.0 * h) - kB * d * d / (h * h);
+    b = 1.0 + 2.0 * kB * d * d / (h * h);
+    c = -d * gd / (6.0 * h) - kB * d * d / (h * h);
+}
+
+// Thomas factors (m, -a m, c' = c m) of every x-line (one thread per row) and
+// y-line (one thread per column), boundary rows closed: wall or sponge = odd
+// mirror of the normal flux (the outside coefficient moves onto the diagonal),
+// maker = the outside value is known (its coefficient goes to cW..cN)
+template <typename T>
+__global__ void k_setup_factors(Dev<T> D, SetupArgs A)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double kB = A.Bd + 1.0 / 3.0;
+    const int nx = D.nx, ny = D.ny;
+    if (t < ny) {
+        const int j = t;
+        double cprev = 0.0;
+        for (int i = 0; i < nx; i++) {
+            double a, b, c;
+            eq21_coef(A.dd[fidx(D, i, j)], A.dd[fidx(D, i - 1, j)], A.dd[fidx(D, i + 1, j)], A.dx, kB, a, b, c);
+            if (i == 0) { A.cW[j] = a; if (A.bt[0] != MAKER) b -= a; a = 0.0; }
+            if (i == nx - 1) { A.cE[j] = c; if (A.bt[1] != MAKER) b -= c; c = 0.0; }
+            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+            const double m = 1.0 / (b - a * cprev);
+            cprev = c * m;
+            const long long o = fidx(D, i, j);
+            D.fxm[o] = (T)m;
+            D.fxe[o] = (T)(-a * m);
+            D.fxc[o] = (T)cprev;
+        }
+    } else if (t < ny + nx) {
+        const int i = t - ny;
+        double cprev = 0.0;
+        for (int j = 0; j < ny; j++) {
+            double a, b, c;
+            eq21_coef(A.dd[fidx(D, i, j)], A.dd[fidx(D, i, j - 1)], A.dd[fidx(D, i, j + 1)], A.dy, kB, a, b, c);
+            if (j == 0) { A.cS[i] = a; if (A.bt[2] != MAKER) b -= a; a = 0.0; }
+            if (j == ny - 1) { A.cN[i] = c; if (A.bt[3] != MAKER) b -= c; c = 0.0; }
+            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+            const double m = 1.0 / (b - a * cprev);
+            cprev = c * m;
+            const long long o = fidx(D, i, j);
+            D.fym[o] = (T)m;
+            D.fye[o] = (T)(-a * m);
+            D.fyc[o] = (T)cprev;
+        }
+    }
+}
+
+// factor fields outside the interior hold the identity row (m = 0, -a m = 1, c' = 0)
+template <typename T>
+__global__ void k_setup_fill(Dev<T> D)
+{
+    const long long n = (long long)D.pitch * (D.ny + 4);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        D.fxe[q] = (T)1;
+        D.fye[q] = (T)1;
+    }
+}
+
+// initial state: w = b + max(d + eta0, 0), P0, Q0 (zeros where not given)
+template <typename T>
+__global__ void k_setup_state(Dev<T> D, SetupArgs A)
+{
+    const long long n = (long long)D.nx * D.ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % D.nx), j = (int)(k / D.nx);
+        const long long c = fidx(D, i, j);
+        const double h = fmax(A.dd[c] + (A.eta0 ? A.eta0[k] : 0.0), 0.0);
+        D.w[0][c] = (T)(A.bCd[c] + h);
+        D.P[c] = (T)(A.P0 ? A.P0[k] : 0.0);
+        D.Q[c] = (T)(A.Q0 ? A.Q0[k] : 0.0);
+    }
+}
+
+template <typename T>
+cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
+{
+    const int gs = 1024;
+    k_setup_fill<T><<<gs, 256, 0, st>>>(D);
+    k_setup_corner<T><<<gs, 256, 0, st>>>(D, A);
+    k_setup_centres<T><<<gs, 256, 0, st>>>(D, A);
+    k_setup_factors<T><<<(D.nx + D.ny + 127) / 128, 128, 0, st>>>(D, A);
+    k_setup_state<T><<<gs, 256, 0, st>>>(D, A);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ utilities
 
 // Eq. 22 rate of the current state (used at creation and after a restore).
@@ -3736,6 +3871,7 @@ cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t 
     template cudaError_t launch_step<T>(const Dev<T> &, cudaStream_t, double);                   \
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
+    template cudaError_t launch_setup<T>(const Dev<T> &, cudaStream_t, const SetupArgs &);       \
     template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
     template int xsolver_staged<T>(const Dev<T> &, int);                                         \
     template int step_launches<T>(const Dev<T> &);                                               \
