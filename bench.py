@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is rec
 # DRAM bytes per launch of the dominant kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (kernel, precision, nx, ny); the capture is summarised under profiles/
-MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.925120e6 + 112.944128e6}
+MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.875968e6 + 113.007872e6}
 # algorithmic bytes per interior cell of each kernel (values it must read +
 # write once), per precision; the whole step in STEP_VALUES
 KERNEL_VALUES = {"fp32": {"rhs_combine": 21, "ysolve": 8, "xsolve": 11},

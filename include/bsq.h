@@ -229,6 +229,15 @@ bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long long max_st
  * shapes change the rounding order of the line solves, not the method. */
 bsq_status bsq_batch_autotune(bsq_batch *b, long long steps_per_trial, int *choice);
 
+/* Replace the batch's members by n other domains (same rules as
+ * bsq_batch_create; precision, Kahan setting and cross mode those of the
+ * batch), keeping its stream, its buffers (grown when needed), its tile shapes
+ * and its executable CUDA graph, which the next bsq_batch_advance updates in
+ * place when the launch sequence allows it.  Waits for the batch's stream
+ * first.  Errors: BSQ_ERR_ARG, BSQ_ERR_OOM, BSQ_ERR_CUDA; on error the batch
+ * must be destroyed. */
+bsq_status bsq_batch_reset(bsq_batch *b, bsq_domain *const *domains, int n);
+
 /* Members of the batch; kernel launches per batched step. */
 int bsq_batch_size(const bsq_batch *b);
 int bsq_batch_launches_per_step(const bsq_batch *b);

@@ -107,6 +107,8 @@ def lib():
         L.bsq_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.bsq_batch_advance.restype = ctypes.c_int
         L.bsq_batch_advance.argtypes = [vp, _DP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.bsq_batch_reset.restype = ctypes.c_int
+        L.bsq_batch_reset.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int]
         L.bsq_batch_size.restype = ctypes.c_int
         L.bsq_batch_size.argtypes = [vp]
         L.bsq_batch_launches_per_step.restype = ctypes.c_int
@@ -405,6 +407,17 @@ class Batch:
         """Per-domain steps taken; t_end is one time for all, a sequence of
         per-domain times, or None (then max_steps > 0)."""
         return bsq_batch_advance(self.h, len(self.domains), t_end, max_steps)
+
+    def reset(self, domains):
+        """Replace the members (bsq_batch_reset): buffers, tile shapes and the
+        executable graph are kept."""
+        domains = list(domains)
+        arr = (ctypes.c_void_p * len(domains))(*[d.h.value if isinstance(d.h, ctypes.c_void_p) else d.h
+                                                  for d in domains])
+        st = lib().bsq_batch_reset(self.h, arr, len(domains))
+        if st != OK:
+            raise BsqError(st, "bsq_batch_reset")
+        self.domains = domains
 
     def launches_per_step(self) -> int:
         return lib().bsq_batch_launches_per_step(self.h)

@@ -296,6 +296,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
+    D.tune_yocc = p.tune[7] & 1;
     D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
@@ -621,8 +622,13 @@ struct bsq_batch {
     std::vector<RhsGroup> rhs_grp;          // descriptors of each RHS launch (single precision)
     std::vector<int> rhs_grp_nb, rhs_grp_off;
     cudaGraphExec_t graph;
+    int graph_stale;     // the block tables changed since the graph was captured
     int graph_steps;
     double timeout_s;
+    size_t dcap;         // bytes of dmem
+    int hcap;            // members the pinned host arrays hold
+    int rows, xk, ky;    // tile shapes of the current tables
+    int kahan, cross;    // the members' Kahan setting and cross mode
 };
 
 static bsq_status wait_batch(const bsq_batch *b)
@@ -664,15 +670,10 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     const int n = (int)b->doms.size();
     std::vector<int4> tg, tr, ts, tc, tx;
     bool fast = true, theta1 = true;
-    if (b->dmem) {
-        cudaStreamSynchronize(b->stream);
-        cudaFree(b->dmem);
-        b->dmem = nullptr;
-    }
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
+    // the tables are rewritten in place: no batched step may still read them
+    // (the graph is captured again before the next launch)
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    b->graph_stale = 1;
     int yrow_max = 32 * K;
     std::vector<Dev<T>> hD(n);
     for (int d = 0; d < n; d++) {
@@ -723,14 +724,31 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     const size_t o_s = take(ts.size() * sizeof(int4)), o_c = take(tc.size() * sizeof(int4));
     const size_t o_x = take(tx.size() * sizeof(int4));
     const size_t o_t = take(n * sizeof(double)), o_ctl = take(n * sizeof(Ctl));
-    if (cudaMalloc(&b->dmem, off) != cudaSuccess) { b->dmem = nullptr; return BSQ_ERR_OOM; }
+    if (off > b->dcap) {
+        // grow (with room), keeping the old buffer until the new one exists
+        void *nm = nullptr;
+        const size_t cap = off + off / 2;
+        if (cudaMalloc(&nm, cap) != cudaSuccess) return BSQ_ERR_OOM;
+        if (b->dmem) cudaFree(b->dmem);
+        b->dmem = nm;
+        b->dcap = cap;
+    }
     char *base = (char *)b->dmem;
-    CK(cudaMemcpy(base + o_D, hD.data(), n * sizeof(Dev<T>), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(base + o_g, tg.data(), tg.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(base + o_r, tr.data(), tr.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(base + o_s, ts.data(), ts.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(base + o_c, tc.data(), tc.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(base + o_x, tx.data(), tx.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    {
+        // descriptors and all tables in one copy
+        std::vector<char> h(o_t);
+        memcpy(h.data() + o_D, hD.data(), n * sizeof(Dev<T>));
+        memcpy(h.data() + o_g, tg.data(), tg.size() * sizeof(int4));
+        memcpy(h.data() + o_r, tr.data(), tr.size() * sizeof(int4));
+        memcpy(h.data() + o_s, ts.data(), ts.size() * sizeof(int4));
+        memcpy(h.data() + o_c, tc.data(), tc.size() * sizeof(int4));
+        memcpy(h.data() + o_x, tx.data(), tx.size() * sizeof(int4));
+        CK(cudaMemcpyAsync(base, h.data(), o_t, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+    }
+    b->rows = rows;
+    b->xk = K;
+    b->ky = KY;
     b->Ds = base + o_D;
     b->d_tend = (double *)(base + o_t);
     b->d_ctl = (Ctl *)(base + o_ctl);
@@ -783,6 +801,8 @@ extern "C" bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *
     if (!b) return BSQ_ERR_OOM;
     b->doms.assign(domains, domains + n);
     b->fp64 = domains[0]->fp64;
+    b->kahan = domains[0]->p.kahan;
+    b->cross = domains[0]->p.cross_mode;
     b->graph_steps = domains[0]->graph_steps;
     b->timeout_s = 0.0;
     for (int d = 0; d < n; d++) {
@@ -804,6 +824,7 @@ extern "C" bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *
         batch_free(b);
         return BSQ_ERR_OOM;
     }
+    b->hcap = n;
     bsq_status st = b->fp64 ? batch_build<double>(b, 64, batch_xchunk<double>(), 8)
                             : batch_build<float>(b, 64, batch_xchunk<float>(), 8);
     if (st != BSQ_OK) {
@@ -812,6 +833,43 @@ extern "C" bsq_status bsq_batch_create(bsq_domain *const *domains, int n, void *
     }
     *out = b;
     return BSQ_OK;
+}
+
+extern "C" bsq_status bsq_batch_reset(bsq_batch *b, bsq_domain *const *domains, int n)
+{
+    cudaGetLastError();
+    if (!b || !domains || n < 1) return BSQ_ERR_ARG;
+    // (the previous members may have been destroyed already: only the batch's
+    // own record of their settings is used)
+    for (int d = 0; d < n; d++) {
+        bsq_domain *x = domains[d];
+        if (!x || x->sticky != BSQ_OK) return BSQ_ERR_ARG;
+        if (x->fp64 != b->fp64 || x->p.kahan != b->kahan || x->p.cross_mode != b->cross) return BSQ_ERR_ARG;
+        for (int e = 0; e < d; e++)
+            if (domains[e] == x) return BSQ_ERR_ARG;
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    if (n > b->hcap) {
+        double *ht = nullptr;
+        Ctl *hc = nullptr;
+        if (cudaMallocHost((void **)&ht, n * sizeof(double)) != cudaSuccess) return BSQ_ERR_OOM;
+        if (cudaMallocHost((void **)&hc, n * sizeof(Ctl)) != cudaSuccess) {
+            cudaFreeHost(ht);
+            return BSQ_ERR_OOM;
+        }
+        cudaFreeHost(b->h_tend);
+        cudaFreeHost(b->h_ctl);
+        b->h_tend = ht;
+        b->h_ctl = hc;
+        b->hcap = n;
+    }
+    b->doms.assign(domains, domains + n);
+    b->timeout_s = 0.0;
+    for (int d = 0; d < n; d++) {
+        const double ts = domains[d]->p.timeout_s > 0 ? domains[d]->p.timeout_s : 600.0;
+        if (ts > b->timeout_s) b->timeout_s = ts;
+    }
+    return b->fp64 ? batch_build<double>(b, b->rows, b->xk, b->ky) : batch_build<float>(b, b->rows, b->xk, b->ky);
 }
 
 extern "C" void bsq_batch_destroy(bsq_batch *b) { batch_free(b); }
@@ -848,7 +906,7 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
     if (st != BSQ_OK) return st;
     std::vector<long long> n0(n);
     for (int d = 0; d < n; d++) n0[d] = b->h_ctl[d].n;
-    if (!b->graph) {
+    if (!b->graph || b->graph_stale) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
@@ -857,9 +915,26 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
                         : launch_batch_step<float>((const Dev<float> *)b->Ds, b->plan, b->stream);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) return BSQ_ERR_CUDA;
-        e = cudaGraphInstantiate(&b->graph, g, 0);
+        // the same launch sequence with new grids and arguments: update the
+        // executable graph in place; otherwise instantiate it again
+        bool updated = false;
+        if (b->graph) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(b->graph, g, &info) == cudaSuccess) {
+                updated = true;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+        }
+        if (!updated) {
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            if (e != cudaSuccess) b->graph = nullptr;
+        }
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) { b->graph = nullptr; return BSQ_ERR_CUDA; }
+        if (!b->graph) return BSQ_ERR_CUDA;
+        b->graph_stale = 0;
     }
     CK(cudaMemcpyAsync(b->d_tend, b->h_tend, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     cudaError_t e = b->fp64

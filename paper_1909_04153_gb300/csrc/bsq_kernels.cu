@@ -1810,8 +1810,8 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
     }
 }
 
-template <typename T, int KY>
-__global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
+template <typename T, int KY, int MB = 1>
+__global__ void __launch_bounds__(256, MB) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
 {
     yapply_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, yin, xaft);
 }
@@ -3555,7 +3555,8 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         // one chunk of 256 adjacent columns per block: each row segment a block
         // reads is 1 KB contiguous
         const dim3 gw((nx + 255) / 256, nch);
-        if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        if (KY == 8 && D.tune_yocc) k_yapply<T, 8, 5><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        else if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
         else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
     } else {
         int CW, NCH, kch;

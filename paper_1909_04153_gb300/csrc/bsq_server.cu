@@ -165,11 +165,18 @@ extern "C" bsq_status bsq_server_poll(bsq_server *s, int *n_running, int *n_pend
     bsq_status ret = BSQ_OK;
     if (!s->running.empty()) {
         if (s->dirty) {
-            bsq_batch_destroy(s->batch);
-            s->batch = nullptr;
+            // the batch is rebuilt in place (buffers and graph reused)
             std::vector<bsq_domain *> doms;
             for (Request *r : s->running) doms.push_back(r->dom);
-            bsq_status st = bsq_batch_create(doms.data(), (int)doms.size(), s->stream, &s->batch);
+            bsq_status st = BSQ_ERR_ARG;
+            if (s->batch) {
+                st = bsq_batch_reset(s->batch, doms.data(), (int)doms.size());
+                if (st != BSQ_OK) {
+                    bsq_batch_destroy(s->batch);
+                    s->batch = nullptr;
+                }
+            }
+            if (!s->batch) st = bsq_batch_create(doms.data(), (int)doms.size(), s->stream, &s->batch);
             if (st != BSQ_OK) return st;
             s->dirty = false;
         }

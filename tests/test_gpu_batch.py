@@ -202,3 +202,26 @@ def test_batch_larger_than_one_rhs_group():
         s.close()
     for d in doms:
         d.close()
+
+
+def test_batch_reset_keeps_members_independent():
+    # bsq_batch_reset swaps members in place (buffers, shapes and graph kept,
+    # the graph updated for the new tables): a member carried over keeps
+    # stepping as if alone, a new member starts as if alone
+    ca, cb, cc = (W.random_basin(96, seed=21, forcing="jonswap"), W.random_basin(64, seed=22),
+                  W.barred_beach(nx=130, ny=70))
+    da, db, dc = (bsq.Domain(c, precision="fp32", graph_steps=8) for c in (ca, cb, cc))
+    with bsq.Batch([da, db]) as b:
+        b.advance(max_steps=20)
+        b.reset([db, dc])
+        done = b.advance(max_steps=20)
+        assert list(done) == [20, 20]
+        assert b.launches_per_step() >= 5
+    sb, n = _alone(cb, "fp32", max_steps=40)
+    sc, m = _alone(cc, "fp32", max_steps=20)
+    assert (n, m) == (40, 20)
+    for f in ("eta", "P", "Q"):
+        np.testing.assert_array_equal(db.read(f), sb.read(f))
+        np.testing.assert_array_equal(dc.read(f), sc.read(f))
+    for d in (da, db, dc, sb, sc):
+        d.close()
