@@ -309,6 +309,9 @@ def run_ours(args):
     served = None
     if rank == 0 and prec == "fp32" and not args.no_served:
         served = run_served(args, dev, stream)
+    fixed_vs_adaptive = None
+    if rank == 0 and prec == "fp32" and not args.no_fixed_study:
+        fixed_vs_adaptive = run_fixed_vs_adaptive(args, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -342,6 +345,7 @@ def run_ours(args):
             "fp64": fp64,
             "batched": batched,
             "served": served,
+            "fixed_vs_adaptive": fixed_vs_adaptive,
             "clocks": clocks,
             "sim": {"t": info["t"], "clamps": info["clamps"]},
         }
@@ -489,6 +493,72 @@ def run_served(args, dev, stream):
     }
 
 
+def run_fixed_vs_adaptive(args, dev, stream):
+    """Adaptive against fixed steps on the rip-channel beach of Eq. 48 (JONSWAP
+    waves, friction), FP32: the adaptive run to T gives its mean, smallest and
+    largest step; fixed-step runs to the same T (cfl = 0, every step dt_init)
+    locate, by bisection, the largest fixed step that stays stable (no
+    non-finite state, |eta| below 1 m)."""
+    import torch
+
+    from paper_1909_04153_gb300 import bsq
+
+    n = args.fixed_study_n
+    T = args.fixed_study_time
+    case = W.hamm_rip(nx=n, ny=n * 3 // 2)
+    p = case["params"]
+    ncell = p["nx"] * p["ny"]
+
+    def run(**over):
+        """Advance to T; (stable, steps, wall seconds, smallest and largest step
+        sampled every 64 steps)."""
+        t0 = time.perf_counter()
+        steps, lo_dt, hi_dt = 0, float("inf"), 0.0
+        try:
+            with bsq.Domain(case, precision="fp32", stream=stream.cuda_stream, **over) as d:
+                while d.info()["t"] < T - 1e-9:
+                    steps += d.advance(t_end=T, max_steps=64)
+                    ldt = d.info()["last_dt"]
+                    lo_dt, hi_dt = min(lo_dt, ldt), max(hi_dt, ldt)
+                eta = d.read("eta")
+                ok = bool(np.isfinite(eta).all() and np.abs(eta).max() < 1.0)
+        except bsq.BsqError:
+            ok = False
+        torch.cuda.synchronize(dev)
+        return ok, steps, time.perf_counter() - t0, lo_dt, hi_dt
+
+    ok, steps_a, wall_a, lo_dt, hi_dt = run()
+    mean_dt = T / steps_a
+    lo, hi = 0.25 * mean_dt, 2.0 * mean_dt
+    trials = []
+    ok_lo = run(cfl=0.0, dt_init=lo)[0]
+    ok_hi = run(cfl=0.0, dt_init=hi)[0]
+    trials += [(lo, ok_lo), (hi, ok_hi)]
+    if ok_lo and not ok_hi:
+        for _ in range(6):
+            mid = 0.5 * (lo + hi)
+            ok_m = run(cfl=0.0, dt_init=mid)[0]
+            trials.append((mid, ok_m))
+            if ok_m:
+                lo = mid
+            else:
+                hi = mid
+    best = lo if ok_lo else None
+    ok_f, steps_f, wall_f = run(cfl=0.0, dt_init=best)[:3] if best else (False, 0, 0.0)
+    return {
+        "workload": "rip-channel beach of Eq. 48, %dx%d, dx %.3g m, JONSWAP Hs 0.13 m Tp 1.6 s, friction 0.0025, "
+                    "FP32, %g s simulated" % (p["nx"], p["ny"], p["dx"], T),
+        "adaptive": {"steps": steps_a, "mean_dt": mean_dt, "min_dt_sampled": lo_dt, "max_dt_sampled": hi_dt,
+                     "cfl": p["cfl"], "wall_s": wall_a, "stable": ok},
+        "largest_stable_fixed_dt": best,
+        "fixed_to_mean_adaptive": (best / mean_dt) if best else None,
+        "fixed": {"steps": steps_f, "wall_s": wall_f, "stable": ok_f},
+        "adaptive_speedup_in_steps": (steps_f / steps_a) if best else None,
+        "trials": [[float(a), bool(b)] for a, b in sorted(trials)],
+        "cells": ncell,
+    }
+
+
 def bsq_bytes_estimate(ncell, fp):
     return ncell * (31 if fp == "fp32" else 28) * (4 if fp == "fp32" else 8)
 
@@ -509,6 +579,9 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-fixed-study", action="store_true")
+    ap.add_argument("--fixed-study-n", type=int, default=500)
+    ap.add_argument("--fixed-study-time", type=float, default=30.0)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-time-scale", type=float, default=0.1)

@@ -70,9 +70,10 @@ typedef struct {
     double dx, dy;         /* cell sizes (m) */
     double g;              /* gravity, 9.81 */
     double Bd;             /* dispersion coefficient B of Eqs. 2-3, 1/15 */
-    double cfl;            /* target CFL of Eq. 22 */
+    double cfl;            /* target CFL of Eq. 22; 0: fixed steps of dt_init (constant-step
+                              AB3, Eqs. 16-18: the weights of Eq. 42 at equal steps) */
     double ema_alpha;      /* alpha of Eq. 47 (0 < alpha <= 1) */
-    double dt_init;        /* first step; <= 0: from Eq. 22 */
+    double dt_init;        /* first step; <= 0: from Eq. 22 (with cfl = 0: every step) */
     double dt_min;         /* a CFL step below this is BSQ_ERR_UNSTABLE */
     double dt_max;         /* upper clamp; <= 0: none */
     double friction;       /* quadratic bottom friction factor f (f1 = f u |u|) */

@@ -296,7 +296,6 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
-    D.tune_yocc = p.tune[7] & 1;
     D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
@@ -411,7 +410,9 @@ extern "C" bsq_status bsq_create(const bsq_params *p, const double *bed_corners,
     *out = nullptr;
     if (!p || !bed_corners) return BSQ_ERR_ARG;
     if (p->nx < 3 || p->ny < 3 || p->nx > 16384 || p->ny > 16384) return BSQ_ERR_ARG;
-    if (!(p->dx > 0) || !(p->dy > 0) || !(p->g > 0) || !(p->cfl > 0) || !(p->ema_alpha > 0) ||
+    // cfl = 0: fixed steps of dt_init (the constant-step AB3 of Eqs. 16-18)
+    if (!(p->cfl >= 0) || (p->cfl == 0 && !(p->dt_init > 0))) return BSQ_ERR_ARG;
+    if (!(p->dx > 0) || !(p->dy > 0) || !(p->g > 0) || !(p->ema_alpha > 0) ||
         p->ema_alpha > 1.0 || p->Bd < 0 || (p->precision != BSQ_FP32 && p->precision != BSQ_FP64) ||
         (p->cross_mode != 0 && p->cross_mode != 1))
         return BSQ_ERR_ARG;

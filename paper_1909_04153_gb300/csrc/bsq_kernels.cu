@@ -257,6 +257,11 @@ __device__ void controller(const Dev<T> &D, double forced_dt, Coef &cf, unsigned
     double dt;
     if (forced_dt > 0.0) {
         dt = forced_dt;
+    } else if (D.cfl <= 0.0) {
+        // fixed step (Eqs. 16-18), landing on t_end
+        dt = D.dt_init;
+        double rem = t_end - t;
+        if (dt > rem) dt = rem;
     } else {
         double rate = bitsd(rb);
         double dtc;
@@ -1234,7 +1239,9 @@ __device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f
 
 constexpr int SW2_COLS = 60;  // interior columns per warp strip (two per lane, lanes 1..30)
 
-template <int YS>
+// FRIC: quadratic bottom friction f1 = f u |u|, f2 = f v |u| (desingularised
+// centre velocities, SURVEY reading A10) in F and G
+template <int YS, bool FRIC = false>
 __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int nstrip, int ROWS)
 {
     typedef float T;
@@ -1412,8 +1419,19 @@ __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int n
             const f2 dispx = fma2(Bgd3, add2(e_xxx, e_xyy), mul2(Bgd2, fma2(ddx, fma2(p2, e_xx, e_yy), mul2(ddy, e_xy))));
             const f2 dispy = fma2(Bgd3, add2(e_yyy, e_xxy), mul2(Bgd2, fma2(ddy, fma2(p2, e_yy, e_xx), mul2(ddx, e_xy))));
             const f2 E = sub2(mul2(divx0, sc2(-1.0f)), divy0);
-            const f2 F = add2(add2(sub2(mul2(divx1, sc2(-1.0f)), divy1), srcx), dispx);
-            const f2 G = add2(add2(sub2(mul2(divx2, sc2(-1.0f)), divy2), srcy), dispy);
+            f2 F = add2(add2(sub2(mul2(divx1, sc2(-1.0f)), divy1), srcx), dispx);
+            f2 G = add2(add2(sub2(mul2(divx2, sc2(-1.0f)), divy2), srcy), dispy);
+            if (FRIC) {
+                const f2 h = max2(sub2(w0, bc), sc2(0.0f));
+                const f2 h2 = mul2(h, h), h4 = mul2(h2, h2);
+                const f2 den = add2(h4, max2(h4, sc2(eps)));
+                const f2 iv = mul2(mul2(sc2((float)BSQ_SQRT2), h), mk2(trsqrt(den.x), trsqrt(den.y)));
+                const f2 u = mul2(iv, P0), v = mul2(iv, Q0);
+                const f2 sp2 = fma2(u, u, mul2(v, v));
+                const f2 fsp = mul2(sc2(D.friction), mk2(tsqrt(sp2.x), tsqrt(sp2.y)));
+                F = sub2(F, mul2(fsp, u));
+                G = sub2(G, mul2(fsp, v));
+            }
             const f2 Q_x = mul2(sub2(Qp, Qm), sc2(half_rdx));
             const f2 Q_y = mul2(sub2(QW[2], QW[0]), sc2(half_rdy));
             const f2 Q_xy = mul2(add2(sub2(sub2(QNp, QSp), QNm), QSm), sc2(q_rdxy));
@@ -1494,10 +1512,10 @@ __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int n
 }
 
 // two blocks of 4 warps per multiprocessor (up to 255 registers a thread)
-template <int YS>
+template <int YS, bool FRIC = false>
 __global__ void __launch_bounds__(128, 2) k_rhs_sw2(Dev<float> D, int nstrip, int rows)
 {
-    rhs_sw2_body<YS>(D, blockIdx.x, nstrip, rows);
+    rhs_sw2_body<YS, FRIC>(D, blockIdx.x, nstrip, rows);
 }
 
 // ------------------------------------------------------------------ y-line solves
@@ -1810,8 +1828,8 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
     }
 }
 
-template <typename T, int KY, int MB = 1>
-__global__ void __launch_bounds__(256, MB) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
+template <typename T, int KY>
+__global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin, const T *xaft)
 {
     yapply_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, yin, xaft);
 }
@@ -3436,7 +3454,11 @@ static bool launch_rhs2(const Dev<float> &D, cudaStream_t st, int rows, int ky)
     const int nstrip = (D.nx + SW2_COLS - 1) / SW2_COLS;
     const int nband = (D.ny + rows - 1) / rows;
     const int blocks = (int)(((long long)nstrip * nband + 3) / 4);
-    if (ky == 16) k_rhs_sw2<16><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+    if (D.friction != 0.0f) {
+        if (ky == 16) k_rhs_sw2<16, true><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+        else if (ky == 8) k_rhs_sw2<8, true><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+        else k_rhs_sw2<0, true><<<blocks, 128, 0, st>>>(D, nstrip, rows);
+    } else if (ky == 16) k_rhs_sw2<16><<<blocks, 128, 0, st>>>(D, nstrip, rows);
     else if (ky == 8) k_rhs_sw2<8><<<blocks, 128, 0, st>>>(D, nstrip, rows);
     else k_rhs_sw2<0><<<blocks, 128, 0, st>>>(D, nstrip, rows);
     return true;
@@ -3479,12 +3501,21 @@ static bool rhs_fast(const Dev<T> &D)
     return D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 && (D.kahan != 0) == (sizeof(T) == 4) &&
            D.fstride * 15 < 0x7fffffffLL;
 }
+// the paired single-precision RHS kernel: the fast configuration, with or
+// without bottom friction
+template <typename T>
+static bool rhs_pair(const Dev<T> &D)
+{
+    const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
+    return sizeof(T) == 4 && D.tune_rhs != 1 && D.tune_rhs1 == 0 && rows != 16 && D.theta == (T)1 &&
+           D.cross_mode != 0 && D.kahan != 0 && D.fstride * 15 < 0x7fffffffLL;
+}
 // 1 when the RHS kernel forms the y-line chunk summaries (no k_ysum launch)
 template <typename T>
 static bool rhs_fuses_ysum(const Dev<T> &D)
 {
     const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
-    return D.tune_rhs != 1 && rhs_fast(D) && D.ysplit && rows != 16 && D.tune_ysum == 0;
+    return D.tune_rhs != 1 && (rhs_fast(D) || rhs_pair(D)) && D.ysplit && rows != 16 && D.tune_ysum == 0;
 }
 
 // One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
@@ -3515,7 +3546,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const bool fast = rhs_fast(D);
         ysum_fused = rhs_fuses_ysum(D);
         const bool t1 = D.theta == (T)1;
-        const bool pair2 = fast && sizeof(T) == 4 && D.tune_rhs1 == 0 && rows != 16;
+        const bool pair2 = rhs_pair(D);
         if (pair2) {
             launch_rhs2(D, st, rows, ysum_fused ? ysplit_rows<T>(D.tune_yk) : 0);
         } else if (fast && ysum_fused) {
@@ -3555,8 +3586,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         // one chunk of 256 adjacent columns per block: each row segment a block
         // reads is 1 KB contiguous
         const dim3 gw((nx + 255) / 256, nch);
-        if (KY == 8 && D.tune_yocc) k_yapply<T, 8, 5><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
-        else if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
         else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
     } else {
         int CW, NCH, kch;

@@ -13,7 +13,10 @@ these generators stand in for them with the same kind of geometry and forcing:
 * ``barred_beach`` -- regular waves over a barred beach cut by three rip
   channels, sponge layers on three sides (the rip-current case of Sec. 5.3);
 * ``random_basin`` -- smooth random bathymetry with solitary or JONSWAP
-  forcing (for many independent domains).
+  forcing (for many independent domains);
+* ``hamm_rip`` -- a plane beach cut by a rip channel, the analytic bathymetry
+  of Eq. 48, irregular JONSWAP waves and quadratic bottom friction (the
+  irregular-wave rip case of Sec. 5.4).
 
 Each returns a dict: ``params`` (nx, ny, dx, dy, bc, ...), ``bed`` ((ny+1, nx+1)
 corner elevations, datum = still water level, so ``w_s = 0``), ``comps``
@@ -157,6 +160,34 @@ def random_basin(n, dx=0.1, seed=SEED, forcing="solitary", sigma_cells=8.0, dmin
                 Q0=None, steps=steps)
 
 
+def hamm_rip_bed(x, y):
+    """Bottom elevation of Eq. 48 (metres above still water): x onshore from the
+    wave maker, y alongshore from the channel centre line."""
+    s = 18.0 - x
+    return 0.1 - s / 30.0 * (1.0 + 3.0 * np.exp(-s / 3.0) * np.cos(np.pi * y / 30.0) ** 10)
+
+
+def hamm_rip(nx=1000, ny=1500, length=20.0, width=30.0, hs=0.13, tp=1.6, gamma=3.3, n_comp=68, f0=None,
+             friction=0.0025, steps=20000, seed=SEED, **kw):
+    """Plane beach with a rip channel (Eq. 48) over x in [0, length], y in
+    [-width/2, width/2] (the channel at y = 0; the plane beach's shoreline at
+    x = 15 m, about 0.5 m of water at the maker); JONSWAP maker on the west
+    side (Hs = 0.13 m, Tp = 1.6 s, 68 components 0.01 Hz apart, seeded
+    phases), quadratic friction f = 0.0025, first step 0.003 s, walls
+    elsewhere.  The full size has the paper's 0.02 m cells."""
+    dx = length / nx
+    dy = width / ny
+    xk = np.arange(nx + 1) * dx
+    yk = np.arange(ny + 1) * dy - 0.5 * width
+    X, Y = np.meshgrid(xk, yk)
+    bed = hamm_rip_bed(X, Y)
+    comps = jonswap_components(hs, tp, gamma, n_comp, f0=f0, seed=seed)
+    kw.setdefault("cfl", 0.125)
+    kw.setdefault("dt_init", 0.003)
+    prm = base_params(nx, ny, dx, dy, bc=(MAKER, WALL, WALL, WALL), ramp_time=5.0 * tp, friction=friction, **kw)
+    return dict(name="hamm_rip", params=prm, bed=bed, comps=comps, eta0=None, P0=None, Q0=None, steps=steps)
+
+
 def batch_sizes(count=64, lo=128, hi=1024, seed=SEED, multiple=32):
     """Side lengths log-uniform in [lo, hi], rounded to a multiple of 32."""
     rng = np.random.default_rng(seed)
@@ -179,6 +210,7 @@ CASES = {
     "solitary_basin": solitary_basin,
     "planar_beach": planar_beach,
     "barred_beach": barred_beach,
+    "hamm_rip": hamm_rip,
 }
 
 

@@ -62,3 +62,19 @@ def test_full_size_adaptive_run_stays_finite_and_conserves_mass():
         h = d.read("h")
         assert np.isfinite(h).all() and (h >= 0).all()
         assert info["n"] == 400 and info["t"] > 0
+
+
+def test_hamm_rip_full_size_adaptive_run():
+    # the rip-channel beach of Eq. 48 at the paper's 0.02 m cells (1000 x 1500),
+    # JONSWAP waves and quadratic friction, advanced adaptively: the first step
+    # is the given 0.003 s, the state stays finite with h >= 0, and later steps
+    # follow the CFL target
+    case = W.make("hamm_rip")
+    with bsq.Domain(case, precision="fp32") as d:
+        d.advance(max_steps=1)
+        assert abs(d.info()["last_dt"] - 0.003) <= 1e-12
+        d.advance(max_steps=600)
+        info = d.info()
+        h = d.read("h")
+        assert np.isfinite(h).all() and (h >= 0).all()
+        assert info["n"] == 601 and 0.0 < info["last_dt"] < 0.003

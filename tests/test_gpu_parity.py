@@ -57,6 +57,7 @@ CASES = {
     "ragged_multi_segment": lambda: _hump_case(301, 37, dx=0.05, seed=5),
     "tall_multi_chunk": lambda: _hump_case(35, 530, dx=0.05, seed=7),
     "random_basin_jonswap": lambda: W.random_basin(64, seed=13, forcing="jonswap"),
+    "hamm_rip_friction": lambda: W.hamm_rip(nx=100, ny=60),
 }
 
 
@@ -104,6 +105,22 @@ def test_fp64_adaptive_dt_trace_matches_oracle():
     np.testing.assert_allclose(got, ref, rtol=1e-8)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_fixed_step_mode_matches_oracle_replay(prec, tol):
+    # cfl = 0: every step is dt_init (the constant-step AB3 of Eqs. 16-18);
+    # the oracle replays the same constant steps, landing on t_end
+    case = CASES["hamm_rip_friction"]()
+    dt, steps = 0.004, 300
+    o = _oracle(case)
+    o.run(steps, dts=[dt] * steps)
+    with bsq.Domain(case, precision=prec, cfl=0.0, dt_init=dt) as d:
+        n = d.advance(t_end=dt * steps)
+        info = d.info()
+        assert n == steps and abs(info["last_dt"] - dt) <= 1e-15
+        assert abs(info["t"] - dt * steps) <= 1e-12
+        assert rel(d.read("eta"), o.get("eta")) <= tol
+
+
 def test_fp64_advance_lands_on_t_end_like_oracle():
     case = W.solitary_basin(nx=64, ny=12)
     o = _oracle(case)
@@ -117,7 +134,7 @@ def test_fp64_advance_lands_on_t_end_like_oracle():
 
 
 @pytest.mark.parametrize("name", ["barred_beach_rips", "hump_2d_walls", "planar_beach_jonswap",
-                                  "random_basin_jonswap"])
+                                  "random_basin_jonswap", "hamm_rip_friction"])
 def test_fp32_kahan_1000_steps_matches_oracle(name):
     case = CASES[name]()
     o = _oracle(case)
