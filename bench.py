@@ -570,7 +570,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="barred_beach", choices=["barred_beach", "planar_beach"])
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--n", "--grid", dest="n", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--graph-steps", type=int, default=16)
     ap.add_argument("--profile-steps", type=int, default=20)
