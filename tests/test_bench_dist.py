@@ -54,7 +54,7 @@ def test_reference_arm_under_torchrun_prints_once():
     env = dict(os.environ, BSQ_BENCH_BACKEND="gloo", MASTER_ADDR="127.0.0.1")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1", "--grid", "48"]
+           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3", "--grid", "48"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
