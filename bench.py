@@ -51,11 +51,20 @@ KERNEL_VALUES = {"fp32": {"rhs_combine": 21, "ysolve": 8, "xsolve": 11},
 STEP_VALUES = {"fp32": 25, "fp64": 19}
 
 
+def case_dims(workload, n):
+    """Grid of the workload at size n: barred beach n x n, planar beach
+    n x n/4, rip-channel beach n x 3n/2 (1000 x 1500 is the 0.02 m grid)."""
+    return {"barred_beach": (n, n), "planar_beach": (n, max(4, n // 4)), "hamm_rip": (n, 3 * n // 2)}[workload]
+
+
 def make_case(workload, n):
+    nx, ny = case_dims(workload, n)
     if workload == "barred_beach":
-        return W.barred_beach(nx=n, ny=n)
+        return W.barred_beach(nx=nx, ny=ny)
     if workload == "planar_beach":
-        return W.planar_beach(nx=n, ny=max(4, n // 4))
+        return W.planar_beach(nx=nx, ny=ny)
+    if workload == "hamm_rip":
+        return W.hamm_rip(nx=nx, ny=ny)
     raise ValueError(workload)
 
 
@@ -204,7 +213,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%s_%dx%d" % (args.workload, args.n, args.n), "sample_grid": [p["nx"], p["ny"]]},
+        "config": {"workload": "%s_%dx%d" % ((args.workload,) + case_dims(args.workload, args.n)),
+                   "sample_grid": [p["nx"], p["ny"]]},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -569,7 +579,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="barred_beach", choices=["barred_beach", "planar_beach"])
+    ap.add_argument("--workload", default="barred_beach", choices=["barred_beach", "planar_beach", "hamm_rip"])
     ap.add_argument("--n", "--grid", dest="n", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--graph-steps", type=int, default=16)

@@ -102,10 +102,14 @@ typedef struct {
                               paired); [7] reserved */
 } bsq_params;
 
+/* Most wave-maker components a domain takes. */
+#define BSQ_MAX_COMP 1024
+
 typedef struct {
     int type[4];               /* BSQ_BC_* per side W, E, S, N */
     double sponge_width[4];    /* band width (m) of sponge sides */
-    int n_comp;                /* wave-maker components (0 if no maker side) */
+    int n_comp;                /* wave-maker components (0 if no maker side; at most
+                                  BSQ_MAX_COMP) */
     const double *amp;         /* amplitude (m) */
     const double *freq;        /* frequency (Hz) */
     const double *phase;       /* phase (rad) */

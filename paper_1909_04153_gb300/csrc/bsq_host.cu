@@ -142,7 +142,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t fb;  // bytes per padded field
     int nfields;
-    size_t o_fields, o_corner, o_gx, o_gy, o_corr, o_cb, o_comp, o_ctl, o_coef, o_mass, o_ysum, total;
+    size_t o_fields, o_corner, o_gx, o_gy, o_corr, o_cb, o_comp, o_mtab, o_ctl, o_coef, o_mass, o_ysum, total;
 };
 constexpr int kMassBlocks = 512;
 
@@ -164,6 +164,10 @@ static Layout layout(int nx, int ny, int tune_xk, bool kahan, int nc)
     L.o_corr = take((size_t)(4 * nx + 4 * ny + 4) * sizeof(T));
     L.o_cb = take((size_t)(2 * nx + 2 * ny) * sizeof(double));
     L.o_comp = take((size_t)7 * (nc > 0 ? nc : 1) * sizeof(double));
+    // single precision: the maker's spatial-phase table, (cos, sin) per component
+    // and maker point (the two ghost layers of all four sides, corners included)
+    const size_t mpts = (size_t)4 * (ny + 4) + (size_t)4 * (nx + 4);
+    L.o_mtab = take(sizeof(T) == 4 && nc > 0 ? mpts * nc * 2 * sizeof(float) : 0);
     L.o_ctl = take(sizeof(Ctl));
     L.o_coef = take(sizeof(Coef));
     L.o_mass = take(kMassBlocks * sizeof(double));
@@ -269,9 +273,9 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     // ---- device memory: one allocation
     const Layout L = layout<T>(nx, ny, p.tune[4], kahan, nc);
     const size_t fb = L.fb;
-    const int nfields = L.nfields;
     const size_t o_fields = L.o_fields, o_corner = L.o_corner, o_gx = L.o_gx, o_gy = L.o_gy, o_corr = L.o_corr;
-    const size_t o_cb = L.o_cb, o_comp = L.o_comp, o_ctl = L.o_ctl, o_coef = L.o_coef, o_mass = L.o_mass;
+    const size_t o_cb = L.o_cb, o_comp = L.o_comp, o_mtab = L.o_mtab, o_ctl = L.o_ctl, o_coef = L.o_coef;
+    const size_t o_mass = L.o_mass;
     const size_t o_ysum = L.o_ysum, off = L.total;
     const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
     const size_t nchy = (size_t)((ysplit_chunks<T>(ny, 8) + 7) & ~7) * nx;
@@ -334,6 +338,8 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.ncomp = nc;
     D.amp = cp; D.om = cp + nc; D.kx = cp + 2 * nc; D.ky = cp + 3 * nc; D.ph = cp + 4 * nc;
     D.cx = cp + 5 * nc; D.cy = cp + 6 * nc;
+    D.mtab = (sizeof(T) == 4 && nc > 0) ? (float2 *)(base + o_mtab) : nullptr;
+    D.mpts = maker_points(D);
     D.ctl = (Ctl *)(base + o_ctl);
     D.coef = (Coef *)(base + o_coef);
     dm->ctl = D.ctl;
@@ -392,6 +398,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     CK(cudaMemcpy(D.gx, gx.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.gy, gy.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
     if (nc > 0) CK(cudaMemcpy(cp, comp.data(), comp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(launch_maker_table<T>(D, dm->stream));
     Ctl c0;
     memset(&c0, 0, sizeof(c0));
     c0.t_end = INFINITY;
@@ -425,7 +432,7 @@ extern "C" bsq_status bsq_create(const bsq_params *p, const double *bed_corners,
         bool maker = false;
         for (int s = 0; s < 4; s++) maker |= b.type[s] == BSQ_BC_MAKER;
         if (maker && (b.n_comp <= 0 || !b.amp || !b.freq || !b.phase || !b.dir)) return BSQ_ERR_ARG;
-        if (b.n_comp < 0) return BSQ_ERR_ARG;
+        if (b.n_comp < 0 || b.n_comp > BSQ_MAX_COMP) return BSQ_ERR_ARG;
     }
     cudaGetLastError();  // a failed call of another domain must not be reported here
     bsq_domain *d = new (std::nothrow) bsq_domain;
@@ -621,7 +628,7 @@ struct bsq_batch {
     Ctl *d_ctl, *h_ctl;  // gathered controller states (h_ctl pinned)
     BatchPlan plan;
     std::vector<RhsGroup> rhs_grp;          // descriptors of each RHS launch (single precision)
-    std::vector<int> rhs_grp_nb, rhs_grp_off;
+    std::vector<int> rhs_grp_nb, rhs_grp_off, x_grp_nb, x_grp_off;
     cudaGraphExec_t graph;
     int graph_stale;     // the block tables changed since the graph was captured
     int graph_steps;
@@ -690,6 +697,8 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     b->rhs_grp.clear();
     b->rhs_grp_nb.clear();
     b->rhs_grp_off.clear();
+    b->x_grp_nb.clear();
+    b->x_grp_off.clear();
     for (int d = 0; d < n; d++) {
         const Dev<T> &D = dev_of<T>(b->doms[d]);
         hD[d] = D;
@@ -715,7 +724,12 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
         const int yrow = (nx + 32 * K - 1) / (32 * K) * (32 * K);
         if (yrow > yrow_max) yrow_max = yrow;
         const int xb = (ny + 3) / 4;
-        for (int q = 0; q < xb; q++) tx.push_back(make_int4(d, q, xb, yrow));
+        if (pair && d % RHS_GROUP == 0) {
+            b->x_grp_off.push_back((int)tx.size());
+            b->x_grp_nb.push_back(0);
+        }
+        for (int q = 0; q < xb; q++) tx.push_back(make_int4(pair ? d % RHS_GROUP : d, q, xb, yrow));
+        if (pair) b->x_grp_nb.back() += xb;
     }
     if ((size_t)4 * yrow_max * sizeof(T) > 96 * 1024) return BSQ_ERR_ARG;  // rows longer than the x-solver holds
     size_t off = 0;
@@ -774,8 +788,12 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     P.rhs_grp = b->rhs_grp.data();
     P.rhs_grp_nb = b->rhs_grp_nb.data();
     P.rhs_grp_off = b->rhs_grp_off.data();
+    P.x_grp_nb = b->x_grp_nb.data();
+    P.x_grp_off = b->x_grp_off.data();
     P.rhs_theta1 = theta1 ? 1 : 0;
     P.yrow_max = yrow_max;
+    P.ncomp_max = 0;
+    for (int d = 0; d < n; d++) P.ncomp_max = hD[d].ncomp > P.ncomp_max ? hD[d].ncomp : P.ncomp_max;
     P.rhs_rows = rows;
     P.xk = K;
     P.ky = KY;
@@ -986,9 +1004,9 @@ extern "C" int bsq_batch_size(const bsq_batch *b) { return b ? (int)b->doms.size
 extern "C" int bsq_batch_launches_per_step(const bsq_batch *b)
 {
     if (!b) return 0;
-    // the fast RHS forms the y-line chunk summaries itself; the paired RHS is one
-    // launch per group of RHS_GROUP domains
-    return (b->plan.rhs_fast ? 5 : 6) + (b->plan.rhs_pair ? b->plan.rhs_ngroups - 1 : 0);
+    // the fast RHS forms the y-line chunk summaries itself; with the paired RHS
+    // the RHS and x-line stages are one launch per group of RHS_GROUP domains
+    return (b->plan.rhs_fast ? 5 : 6) + (b->plan.rhs_pair ? 2 * (b->plan.rhs_ngroups - 1) : 0);
 }
 
 // Try every tile-shape combination on the batch itself (real steps), keep the

@@ -84,6 +84,8 @@ struct Dev {
     // wave maker
     int ncomp;
     const double *amp, *om, *kx, *ky, *ph, *cx, *cy;
+    float2 *mtab;             // single precision: cos and sin of each component's spatial phase at
+    int mpts;                 // the mpts maker points, [component][point] (null without a maker)
     // controller
     Ctl *ctl;
     Coef *coef;
@@ -119,13 +121,23 @@ struct BatchPlan {
     const int4 *t_ghost, *t_rhs, *t_ysum, *t_yscan, *t_x;
     int rhs_fast, rhs_theta1;                     // RHS variant shared by all domains
     int rhs_pair;                                 // single precision: two columns per lane (k_rhs_sw2 body)
-    int rhs_ngroups;                              // with rhs_pair: launches of the RHS stage, and per
-    const RhsGroup *rhs_grp;                      // launch (host arrays) its descriptors, blocks and
-    const int *rhs_grp_nb, *rhs_grp_off;          // first entry in t_rhs
+    int rhs_ngroups;                              // with rhs_pair: launches of the RHS and x-line
+    const RhsGroup *rhs_grp;                      // stages, and per launch (host arrays) its
+    const int *rhs_grp_nb, *rhs_grp_off;          // descriptors, blocks and first entry in t_rhs
+    const int *x_grp_nb, *x_grp_off;              // and in t_x
     int yrow_max;                                 // x-solver shared row length (elements)
+    int ncomp_max;                                // most wave-maker components of a domain
     int rhs_rows, xk, ky;                         // tile shapes: RHS rows per warp, x elements per
                                                   // lane, y rows per chunk (the autotuner's knobs)
 };
+
+// Maker points of the single-precision maker table: two ghost layers on each
+// of the four sides, each layer two cells longer than the side at either end.
+template <typename T>
+__host__ __device__ inline int maker_points(const Dev<T> &D)
+{
+    return 4 * (D.ny + 4) + 4 * (D.nx + 4);
+}
 
 template <typename T>
 __host__ __device__ inline long long fidx(const Dev<T> &D, int i, int j)

@@ -158,22 +158,15 @@ __device__ __forceinline__ void sincos_phase_f(double ph, float &s, float &c)
     c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
 }
 
-// Linear wave-maker state (eta, P, Q) at (x, y, t) with ramp value r, in FP64.
+// Linear wave-maker state (eta, P, Q) at (x, y, t) with ramp value r, in FP64
+// (the double-precision path).
 template <typename T>
 __device__ void maker_state(const Dev<T> &D, double x, double y, double t, double r, double &e, double &p, double &q)
 {
     double se = 0.0, sp = 0.0, sq = 0.0;
     for (int k = 0; k < D.ncomp; k++) {
         const double ph = D.kx[k] * x + D.ky[k] * y - D.om[k] * t + D.ph[k];
-        double c;
-        if (sizeof(T) == 4) {
-            float sf, cf;
-            sincos_phase_f(ph, sf, cf);
-            c = (double)cf;
-        } else {
-            c = cos(ph);
-        }
-        double ek = D.amp[k] * c;
+        const double ek = D.amp[k] * cos(ph);
         se += ek;
         sp += D.cx[k] * ek;
         sq += D.cy[k] * ek;
@@ -184,44 +177,122 @@ __device__ void maker_state(const Dev<T> &D, double x, double y, double t, doubl
 }
 
 // Increments of the maker fluxes from (t0, r0) to (t1, r1) at (x, y), and Q
-// at t1.  They enter the boundary rows of the line systems as -A (g^{n+1} - g^n),
-// a small difference of two maker values; in single precision it is formed
-// from the identity
-//   r1 cos(ph0 + d) - r0 cos(ph0) = cos(ph0) ((r1 - r0) + r1 (cos d - 1)) - r1 sin(ph0) sin d,
-// d = -omega (t1 - t0), with sin d and cos d - 1 from their Taylor series, so
-// the increment keeps single-precision relative accuracy instead of the
-// absolute error of two cosines.
+// at t1, in FP64.  They enter the boundary rows of the line systems as
+// -A (g^{n+1} - g^n).
 template <typename T>
 __device__ void maker_increment(const Dev<T> &D, double x, double y, double t0, double t1, double r0, double r1,
                                 double &dp, double &dq, double &q1)
 {
-    if (sizeof(T) == 8) {
-        double e0, p0, q0, e1, p1;
-        maker_state(D, x, y, t0, r0, e0, p0, q0);
-        maker_state(D, x, y, t1, r1, e1, p1, q1);
-        dp = p1 - p0;
-        dq = q1 - q0;
-        return;
+    double e0, p0, q0, e1, p1;
+    maker_state(D, x, y, t0, r0, e0, p0, q0);
+    maker_state(D, x, y, t1, r1, e1, p1, q1);
+    dp = p1 - p0;
+    dq = q1 - q0;
+}
+
+// ---- the single-precision maker
+//
+// A component's phase kx x + ky y + phi - omega t splits into a spatial part,
+// fixed at every point where the maker is evaluated, and a temporal part
+// shared by all points.  The spatial part's cos and sin are tabulated once at
+// set-up (FP64, rounded to FP32; k_setup_mtab), the temporal part's once per
+// step and block in shared memory (maker_step), and a point's value is the
+// rotation  cos(s + t) = cos s cos t - sin s sin t  in FP32: no FP64
+// arithmetic per point and component.
+//
+// Maker points: the two ghost layers (g = 1, 2) of each side, each over the
+// side's length plus two cells past either end, W from 0, E from 2 (ny + 4),
+// S from 4 (ny + 4), N from 4 (ny + 4) + 2 (nx + 4); the boundary points of
+// the line systems are the cells of layer 1.  Table layout [component][point].
+template <typename T>
+__device__ __forceinline__ int maker_point(const Dev<T> &D, int side, int i, int j)
+{
+    const int ly = D.ny + 4, lx = D.nx + 4;
+    if (side == SW) return (-i - 1) * ly + j + 2;
+    if (side == SE) return 2 * ly + (i - D.nx) * ly + j + 2;
+    if (side == SS) return 4 * ly + (-j - 1) * lx + i + 2;
+    return 4 * ly + 2 * lx + (j - D.ny) * lx + i + 2;
+}
+
+// Per-component factors of one step: cos and sin of -omega t, sin d and
+// cos d - 1 of d = -omega (t_next - t) from their Taylor series (|d| is a
+// small fraction of a radian at any stable step), and a, a cx, a cy.
+struct MakerStep {
+    const float *ct, *st, *sd, *cm1, *a, *ax, *ay;
+};
+
+// Shared-memory bytes of maker_step for a domain with nc components.
+__host__ __device__ constexpr int maker_step_bytes(int nc) { return 7 * nc * (int)sizeof(float); }
+
+// Fills the factors for the calling block (all its threads take part; one
+// __syncthreads).  Dynamic shared memory of maker_step_bytes(ncomp).
+template <typename T>
+__device__ MakerStep maker_step(const Dev<T> &D, double t, double t_next)
+{
+    extern __shared__ float maker_sm[];
+    const int nc = D.ncomp;
+    float *ct = maker_sm, *st = ct + nc, *sd = st + nc, *cm1 = sd + nc, *a = cm1 + nc, *ax = a + nc, *ay = ax + nc;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        float s, c;
+        sincos_phase_f(-D.om[k] * t, s, c);
+        ct[k] = c;
+        st[k] = s;
+        const float d = (float)(-D.om[k] * (t_next - t)), d2 = d * d;
+        sd[k] = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
+        cm1[k] = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+        const float ak = (float)D.amp[k];
+        a[k] = ak;
+        ax[k] = (float)D.cx[k] * ak;
+        ay[k] = (float)D.cy[k] * ak;
     }
-    float sp = 0.0f, sq = 0.0f, sq1 = 0.0f;
-    const float dr = (float)(r1 - r0), r1f = (float)r1;
+    __syncthreads();
+    return MakerStep{ct, st, sd, cm1, a, ax, ay};
+}
+
+// Maker state (eta, P, Q) at maker point pt and the factors' time, ramp r.
+__device__ __forceinline__ void maker_state_tab(const Dev<float> &D, const MakerStep &m, int pt, float r, float &e,
+                                                float &p, float &q)
+{
+    float se = 0.0f, sp = 0.0f, sq = 0.0f;
+    const float2 *tb = D.mtab + pt;
+#pragma unroll 8  // eight table loads in flight per point
     for (int k = 0; k < D.ncomp; k++) {
-        const double ph0 = D.kx[k] * x + D.ky[k] * y - D.om[k] * t0 + D.ph[k];
-        float s0, c0;
-        sincos_phase_f(ph0, s0, c0);
-        const float d = (float)(-D.om[k] * (t1 - t0)), d2 = d * d;
-        const float sd = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-        const float cm1 = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
-        const float term = c0 * (dr + r1f * cm1) - r1f * s0 * sd;
-        const float c1 = c0 + (c0 * cm1 - s0 * sd);
-        const float a = (float)D.amp[k];
-        sp += (float)D.cx[k] * a * term;
-        sq += (float)D.cy[k] * a * term;
-        sq1 += (float)D.cy[k] * a * c1;
+        const float2 cs = tb[(size_t)k * D.mpts];
+        const float c = cs.x * m.ct[k] - cs.y * m.st[k];
+        se += m.a[k] * c;
+        sp += m.ax[k] * c;
+        sq += m.ay[k] * c;
     }
-    dp = (double)sp;
-    dq = (double)sq;
-    q1 = (double)(r1f * sq1);
+    e = r * se;
+    p = r * sp;
+    q = r * sq;
+}
+
+// Increments of the maker fluxes at maker point pt from (t, r0) to
+// (t_next, r1), and Q at t_next.  The increment is a small difference of
+// two maker values; it is formed from the identity
+//   r1 cos(ph0 + d) - r0 cos(ph0) = cos(ph0) ((r1 - r0) + r1 (cos d - 1)) - r1 sin(ph0) sin d
+// so that it keeps single-precision relative accuracy instead of the
+// absolute error of two cosines.
+__device__ __forceinline__ void maker_increment_tab(const Dev<float> &D, const MakerStep &m, int pt, float dr,
+                                                    float r1, float &dp, float &dq, float &q1)
+{
+    float sp = 0.0f, sq = 0.0f, sq1 = 0.0f;
+    const float2 *tb = D.mtab + pt;
+#pragma unroll 8  // eight table loads in flight per point
+    for (int k = 0; k < D.ncomp; k++) {
+        const float2 cs = tb[(size_t)k * D.mpts];
+        const float c0 = cs.x * m.ct[k] - cs.y * m.st[k];
+        const float s0 = cs.y * m.ct[k] + cs.x * m.st[k];
+        const float term = c0 * (dr + r1 * m.cm1[k]) - r1 * s0 * m.sd[k];
+        const float c1 = c0 + (c0 * m.cm1[k] - s0 * m.sd[k]);
+        sp += m.ax[k] * term;
+        sq += m.ay[k] * term;
+        sq1 += m.ay[k] * c1;
+    }
+    dp = sp;
+    dq = sq;
+    q1 = r1 * sq1;
 }
 
 // ------------------------------------------------------------------ controller
@@ -346,8 +417,11 @@ template <> __device__ __forceinline__ double coefv<double>(const Coef &c, int w
 // Value of ghost cell (i, j) from the current interior: the W/E columns are
 // filled first (mirror with P negated, or the maker), then the S/N rows from
 // the filled columns (mirror with Q negated, or the maker).
+// The single-precision path evaluates the maker from the table with the
+// step factors m (filled for time t); the double-precision path directly.
 template <typename T>
-__device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t, double ramp, T &gw, T &gP, T &gQ)
+__device__ void ghost_value(const Dev<T> &D, const MakerStep &m, const T *w, int i, int j, double t, double ramp,
+                            T &gw, T &gP, T &gQ)
 {
     int nx = D.nx, ny = D.ny;
     int side = -1;
@@ -370,15 +444,21 @@ __device__ void ghost_value(const Dev<T> &D, const T *w, int i, int j, double t,
         }
     }
     if (side >= 0) {
-        double e, p, q;
-        maker_state(D, ((double)i + 0.5) * D.dxd, ((double)j + 0.5) * D.dyd, t, ramp, e, p, q);
-        long long c = fidx(D, i, j);
+        // a maker cell; a corner cell next to a mirrored S/N side is the mirror
+        // (Q negated) of the maker column cell (i, sj) it faces
+        T e, p, q;
+        if constexpr (sizeof(T) == 4) {
+            maker_state_tab(D, m, maker_point(D, side, i, sj), (float)ramp, e, p, q);
+        } else {
+            maker_state(D, ((double)i + 0.5) * D.dxd, ((double)sj + 0.5) * D.dyd, t, ramp, e, p, q);
+        }
+        long long c = fidx(D, i, sj);
         T b = D.bC[c];
         T d = tmax(D.w_s - b, (T)0);
-        T h = tmax(d + (T)e, (T)0);
+        T h = tmax(d + e, (T)0);
         gw = b + h;
-        gP = (T)p;
-        gQ = (T)q;
+        gP = p;
+        gQ = flipQ ? -q : q;
         return;
     }
     long long c = fidx(D, si, sj);
@@ -395,6 +475,10 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
     const Coef scf = *D.coef;
     if (!scf.active) return;
     const double t0 = scf.t0, t1 = scf.t1, r0 = scf.ramp0, r1 = scf.ramp1;
+    MakerStep m{};
+    if constexpr (sizeof(T) == 4) {
+        if (D.ncomp > 0) m = maker_step(D, t0, t1);  // block-uniform
+    }
     int nx = D.nx, ny = D.ny;
     T *w = D.w[scf.wc];
     // 32-bit index arithmetic: the perimeter work is far below 2^31 items
@@ -407,7 +491,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
             int g = rem / ny + 1, j = rem - (g - 1) * ny;
             int i = side == 0 ? -g : nx - 1 + g;
             T a, b, c;
-            ghost_value(D, w, i, j, t0, r0, a, b, c);
+            ghost_value(D, m, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else if (idx < nghost) {
@@ -417,7 +501,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
             int g = rem / (nx + 4) + 1, i = rem - (g - 1) * (nx + 4) - 2;
             int j = side == 0 ? -g : ny - 1 + g;
             T a, b, c;
-            ghost_value(D, w, i, j, t0, r0, a, b, c);
+            ghost_value(D, m, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else {
@@ -428,10 +512,17 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                 int s = side == 0 ? SW : SE;
                 T corr = (T)0;
                 if (D.bc[s] == MAKER) {
-                    double x = side == 0 ? -0.5 * D.dxd : ((double)nx + 0.5) * D.dxd;
-                    double y = ((double)j + 0.5) * D.dyd;
                     double dp, dq, q1;
-                    maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
+                    if constexpr (sizeof(T) == 4) {
+                        float fp, fq, fq1;
+                        maker_increment_tab(D, m, maker_point(D, s, side == 0 ? -1 : nx, j), (float)(r1 - r0),
+                                            (float)r1, fp, fq, fq1);
+                        dp = fp; dq = fq; q1 = fq1;
+                    } else {
+                        double x = side == 0 ? -0.5 * D.dxd : ((double)nx + 0.5) * D.dxd;
+                        double y = ((double)j + 0.5) * D.dyd;
+                        maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
+                    }
                     double a = side == 0 ? D.cW[j] : D.cE[j];
                     corr = (T)(-a * dp);
                     (side == 0 ? D.mqW : D.mqE)[j] = (T)q1;
@@ -443,17 +534,32 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                 int s = side == 0 ? SS : SN;
                 T corr = (T)0;
                 if (D.bc[s] == MAKER) {
+                    const int jg = side == 0 ? -1 : ny;
                     double x = ((double)i + 0.5) * D.dxd;
-                    double y = side == 0 ? -0.5 * D.dyd : ((double)ny + 0.5) * D.dyd;
-                    double dp, dq, q1, e1, p1;
-                    maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
+                    double y = ((double)jg + 0.5) * D.dyd;
+                    double dp, dq, q1;
+                    if constexpr (sizeof(T) == 4) {
+                        float fp, fq, fq1;
+                        maker_increment_tab(D, m, maker_point(D, s, i, jg), (float)(r1 - r0), (float)r1, fp, fq, fq1);
+                        dp = fp; dq = fq; q1 = fq1;
+                    } else {
+                        maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
+                    }
                     double a = side == 0 ? D.cS[i] : D.cN[i];
                     corr = (T)(-a * dq);
                     (side == 0 ? D.mqS : D.mqN)[i + 1] = (T)q1;
                     if (i == 0 || i == nx - 1) {
                         // the corner columns -1 and nx of the ghost row
                         const int ic = i == 0 ? -1 : nx;
-                        maker_state(D, ((double)ic + 0.5) * D.dxd, y, t1, r1, e1, p1, q1);
+                        if constexpr (sizeof(T) == 4) {
+                            float fp, fq, fq1;
+                            maker_increment_tab(D, m, maker_point(D, s, ic, jg), (float)(r1 - r0), (float)r1, fp, fq,
+                                                fq1);
+                            q1 = fq1;
+                        } else {
+                            double e1, p1;
+                            maker_state(D, ((double)ic + 0.5) * D.dxd, y, t1, r1, e1, p1, q1);
+                        }
                         (side == 0 ? D.mqS : D.mqN)[ic + 1] = (T)q1;
                     }
                 }
@@ -475,6 +581,10 @@ __global__ void __launch_bounds__(256) k_ghost_q(Dev<T> D)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
+    MakerStep m{};
+    if constexpr (sizeof(T) == 4) {
+        if (D.ncomp > 0) m = maker_step(D, cf.t1, cf.t1);  // block-uniform
+    }
     int nx = D.nx, ny = D.ny;
     long long nghost = 4LL * ny + 4LL * (nx + 4);
     T *w = D.w[cf.wc ^ 1];
@@ -496,7 +606,7 @@ __global__ void __launch_bounds__(256) k_ghost_q(Dev<T> D)
             j = side == 0 ? -g : ny - 1 + g;
         }
         T a, b, c;
-        ghost_value(D, w, i, j, cf.t1, cf.ramp1, a, b, c);
+        ghost_value(D, m, w, i, j, cf.t1, cf.ramp1, a, b, c);
         D.Q[fidx(D, i, j)] = c;
     }
 }
@@ -3276,6 +3386,48 @@ cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
     return cudaGetLastError();
 }
 
+// Table of the single-precision maker: cos and sin of kx x + ky y + phi of
+// every component at every maker point of the maker sides (FP64, rounded to
+// FP32); one thread per (component, point).
+__global__ void k_setup_mtab(Dev<float> D)
+{
+    const int nx = D.nx, ny = D.ny, ly = ny + 4, lx = nx + 4, np = D.mpts;
+    const long long n = (long long)np * D.ncomp;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q / np), pt = (int)(q - (long long)k * np);
+        int side, r;
+        if (pt < 2 * ly) { side = SW; r = pt; }
+        else if (pt < 4 * ly) { side = SE; r = pt - 2 * ly; }
+        else if (pt < 4 * ly + 2 * lx) { side = SS; r = pt - 4 * ly; }
+        else { side = SN; r = pt - 4 * ly - 2 * lx; }
+        if (D.bc[side] != MAKER) continue;
+        const int len = side == SW || side == SE ? ly : lx;
+        const int g = r / len + 1, m = r - (g - 1) * len - 2;
+        int i, j;
+        if (side == SW) { i = -g; j = m; }
+        else if (side == SE) { i = nx - 1 + g; j = m; }
+        else if (side == SS) { i = m; j = -g; }
+        else { i = m; j = ny - 1 + g; }
+        const double ph = D.kx[k] * (((double)i + 0.5) * D.dxd) + D.ky[k] * (((double)j + 0.5) * D.dyd) + D.ph[k];
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        D.mtab[q] = make_float2((float)cs, (float)sn);
+    }
+}
+
+template <typename T>
+cudaError_t launch_maker_table(const Dev<T> &D, cudaStream_t st)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (D.mtab && D.ncomp > 0) {
+            const long long n = (long long)D.mpts * D.ncomp;
+            const int blocks = (int)(n / 256 + 1 < 4096 ? n / 256 + 1 : 4096);
+            k_setup_mtab<<<blocks, 256, 0, st>>>(D);
+        }
+    }
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ utilities
 
 // Eq. 22 rate of the current state (used at creation and after a restore).
@@ -3518,6 +3670,14 @@ static bool rhs_fuses_ysum(const Dev<T> &D)
     return D.tune_rhs != 1 && (rhs_fast(D) || rhs_pair(D)) && D.ysplit && rows != 16 && D.tune_ysum == 0;
 }
 
+// Dynamic shared memory of the ghost kernels: the single-precision maker's
+// per-step factors.
+template <typename T>
+static int ghost_smem(const Dev<T> &D)
+{
+    return sizeof(T) == 4 ? maker_step_bytes(D.ncomp) : 0;
+}
+
 // One step on stream st: ghost cells, RHS + combine, y-line solves, (ghost
 // cells of Q where the x-solver does not patch them itself), x-line solves
 // whose last block runs the controller of the next step with forced_dt_next
@@ -3531,7 +3691,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     int gb = (int)((nwork + 255) / 256);
     bool ysum_fused = false;  // the RHS kernel forms the y-line chunk summaries
     if (ev) cudaEventRecord(ev[0], st);
-    k_ghost<T><<<gb, 256, 0, st>>>(D);
+    k_ghost<T><<<gb, 256, ghost_smem(D), st>>>(D);
     if (ev) cudaEventRecord(ev[1], st);
     if (D.tune_rhs == 1) {
         constexpr int TX = 32, TY = 8;
@@ -3608,7 +3768,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     const bool tma = xwarp || grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
     if (D.cross_mode != 0 && !tma) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
-        k_ghost_q<T><<<(int)((ng + 255) / 256), 256, 0, st>>>(D);
+        k_ghost_q<T><<<(int)((ng + 255) / 256), 256, ghost_smem(D), st>>>(D);
     }
     if (ev) cudaEventRecord(ev[4], st);
     if (xwarp) {
@@ -3823,6 +3983,15 @@ int batch_xchunk()
     return sizeof(T) == 4 ? 8 : 4;
 }
 
+// table entry: (domain within the group, block of that domain, that domain's
+// block count, its y row length); the group's descriptors are a kernel parameter
+template <int K>
+__global__ void __launch_bounds__(32 * XW_WARPS, 4) k_xsolve_warp_g(const __grid_constant__ RhsGroup G, const int4 *tab)
+{
+    const int4 e = tab[blockIdx.x];
+    xsolve_warp_body<float, K>(G.d[e.x], e.y, (unsigned)e.z, e.w, 0.0);
+}
+
 template <typename T>
 cudaError_t configure_batch(int yrow_max)
 {
@@ -3830,6 +3999,12 @@ cudaError_t configure_batch(int yrow_max)
     cudaError_t e = cudaFuncSetAttribute(k_xsolve_warp_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_warp_b<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if constexpr (sizeof(T) == 4) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_xsolve_warp_g<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_xsolve_warp_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
     return e;
 }
 
@@ -3864,7 +4039,7 @@ static void launch_batch_rhs(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t 
 template <typename T>
 cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t st)
 {
-    k_ghost_b<T><<<P.nb_ghost, 256, 0, st>>>(Ds, P.t_ghost);
+    k_ghost_b<T><<<P.nb_ghost, 256, sizeof(T) == 4 ? maker_step_bytes(P.ncomp_max) : 0, st>>>(Ds, P.t_ghost);
     if (P.rhs_rows == 32) launch_batch_rhs<T, 32>(Ds, P, st);
     else launch_batch_rhs<T, 64>(Ds, P, st);
     if (!P.rhs_fast) {  // (the fast RHS forms the chunk summaries itself)
@@ -3875,6 +4050,17 @@ cudaError_t launch_batch_step(const Dev<T> *Ds, const BatchPlan &P, cudaStream_t
     if (P.ky == 16) k_yapply_b<T, 16><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
     else k_yapply_b<T, 8><<<P.nb_ysum, dim3(32, 8), 0, st>>>(Ds, P.t_ysum);
     const size_t xs = (size_t)XW_WARPS * P.yrow_max * sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+        if (P.rhs_pair) {
+            // descriptors as a kernel parameter, one launch per group (as the RHS stage)
+            for (int g = 0; g < P.rhs_ngroups; g++) {
+                const int4 *tab = P.t_x + P.x_grp_off[g];
+                if (P.xk == 8) k_xsolve_warp_g<8><<<P.x_grp_nb[g], 32 * XW_WARPS, xs, st>>>(P.rhs_grp[g], tab);
+                else k_xsolve_warp_g<4><<<P.x_grp_nb[g], 32 * XW_WARPS, xs, st>>>(P.rhs_grp[g], tab);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (P.xk == 8) k_xsolve_warp_b<T, 8><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
     else k_xsolve_warp_b<T, 4><<<P.nb_x, 32 * XW_WARPS, xs, st>>>(Ds, P.t_x);
     return cudaGetLastError();
@@ -3903,6 +4089,7 @@ cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t 
     template cudaError_t launch_step_timed<T>(const Dev<T> &, cudaStream_t, double, cudaEvent_t *);\
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
     template cudaError_t launch_setup<T>(const Dev<T> &, cudaStream_t, const SetupArgs &);       \
+    template cudaError_t launch_maker_table<T>(const Dev<T> &, cudaStream_t);                    \
     template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
     template int xsolver_staged<T>(const Dev<T> &, int);                                         \
     template int step_launches<T>(const Dev<T> &);                                               \

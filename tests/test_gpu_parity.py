@@ -49,6 +49,18 @@ def _hump_case(nx, ny, dx=0.1, seed=3):
     return dict(params=W.base_params(nx, ny, dx, cfl=0.125), bed=bed, comps=None, eta0=eta, P0=None, Q0=None)
 
 
+def _maker_case(nx, ny, bc, seed, dx=0.1):
+    # oblique multi-component makers (directions seeded in +-0.7 rad) on the
+    # given sides: every side's ghost layers, the corners and the boundary rows
+    # of both line directions take maker values
+    bed = _smooth_bed(nx, ny, dx, seed, lo=0.4, hi=0.9)
+    comps = W.jonswap_components(0.02, 1.2, n=16, seed=seed)
+    comps[:, 3] = np.random.default_rng(seed + 1).uniform(-0.7, 0.7, size=len(comps))
+    sw = tuple(1.5 if b == W.SPONGE else 0.0 for b in bc)
+    prm = W.base_params(nx, ny, dx, bc=bc, sponge_width=sw, ramp_time=2.0, cfl=0.125)
+    return dict(params=prm, bed=bed, comps=comps, eta0=None, P0=None, Q0=None)
+
+
 CASES = {
     "hump_2d_walls": lambda: _hump_case(77, 45),
     "barred_beach_rips": lambda: W.barred_beach(nx=96, ny=72),
@@ -58,6 +70,8 @@ CASES = {
     "tall_multi_chunk": lambda: _hump_case(35, 530, dx=0.05, seed=7),
     "random_basin_jonswap": lambda: W.random_basin(64, seed=13, forcing="jonswap"),
     "hamm_rip_friction": lambda: W.hamm_rip(nx=100, ny=60),
+    "makers_four_sides_oblique": lambda: _maker_case(70, 58, (W.MAKER,) * 4, seed=21),
+    "makers_west_east_oblique": lambda: _maker_case(83, 47, (W.MAKER, W.MAKER, W.WALL, W.SPONGE), seed=23),
 }
 
 
@@ -134,7 +148,8 @@ def test_fp64_advance_lands_on_t_end_like_oracle():
 
 
 @pytest.mark.parametrize("name", ["barred_beach_rips", "hump_2d_walls", "planar_beach_jonswap",
-                                  "random_basin_jonswap", "hamm_rip_friction"])
+                                  "random_basin_jonswap", "hamm_rip_friction", "makers_four_sides_oblique",
+                                  "makers_west_east_oblique"])
 def test_fp32_kahan_1000_steps_matches_oracle(name):
     case = CASES[name]()
     o = _oracle(case)
