@@ -216,37 +216,55 @@ __device__ __forceinline__ int maker_point(const Dev<T> &D, int side, int i, int
 
 // Per-component factors of one step: cos and sin of -omega t, sin d and
 // cos d - 1 of d = -omega (t_next - t) from their Taylor series (|d| is a
-// small fraction of a radian at any stable step), and a, a cx, a cy.
+// small fraction of a radian at any stable step), and a, a cx, a cy; two
+// float4 per component, f[2k] = (cos, sin, sin d, cos d - 1) and
+// f[2k + 1] = (a, a cx, a cy, 0).
 struct MakerStep {
-    const float *ct, *st, *sd, *cm1, *a, *ax, *ay;
+    const float4 *f;
 };
 
 // Shared-memory bytes of maker_step for a domain with nc components.
-__host__ __device__ constexpr int maker_step_bytes(int nc) { return 7 * nc * (int)sizeof(float); }
+__host__ __device__ constexpr int maker_step_bytes(int nc) { return 2 * nc * (int)sizeof(float4); }
 
 // Fills the factors for the calling block (all its threads take part; one
 // __syncthreads).  Dynamic shared memory of maker_step_bytes(ncomp).
 template <typename T>
 __device__ MakerStep maker_step(const Dev<T> &D, double t, double t_next)
 {
-    extern __shared__ float maker_sm[];
-    const int nc = D.ncomp;
-    float *ct = maker_sm, *st = ct + nc, *sd = st + nc, *cm1 = sd + nc, *a = cm1 + nc, *ax = a + nc, *ay = ax + nc;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    extern __shared__ float4 maker_sm[];
+    for (int k = threadIdx.x; k < D.ncomp; k += blockDim.x) {
         float s, c;
         sincos_phase_f(-D.om[k] * t, s, c);
-        ct[k] = c;
-        st[k] = s;
         const float d = (float)(-D.om[k] * (t_next - t)), d2 = d * d;
-        sd[k] = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-        cm1[k] = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+        const float sd = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
+        const float cm1 = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
         const float ak = (float)D.amp[k];
-        a[k] = ak;
-        ax[k] = (float)D.cx[k] * ak;
-        ay[k] = (float)D.cy[k] * ak;
+        maker_sm[2 * k] = make_float4(c, s, sd, cm1);
+        maker_sm[2 * k + 1] = make_float4(ak, (float)D.cx[k] * ak, (float)D.cy[k] * ak, 0.0f);
     }
     __syncthreads();
-    return MakerStep{ct, st, sd, cm1, a, ax, ay};
+    return MakerStep{maker_sm};
+}
+
+// The table is read in batches of MK_BATCH components, all loads of a batch
+// issued before their use: a point's sum is a chain of load latencies, one
+// per batch (a handful of points per block, so little else hides them).  The
+// loads carry an L2 evict-last policy, so the table (a few MB, read every
+// step) tends to stay in L2 while the step's streaming kernels pass through.
+constexpr int MK_BATCH = 32;
+
+__device__ __forceinline__ unsigned long long l2_keep_policy()
+{
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ float2 ld_keep(const float2 *p, unsigned long long pol)
+{
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
 }
 
 // Maker state (eta, P, Q) at maker point pt and the factors' time, ramp r.
@@ -255,13 +273,23 @@ __device__ __forceinline__ void maker_state_tab(const Dev<float> &D, const Maker
 {
     float se = 0.0f, sp = 0.0f, sq = 0.0f;
     const float2 *tb = D.mtab + pt;
-#pragma unroll 8  // eight table loads in flight per point
-    for (int k = 0; k < D.ncomp; k++) {
-        const float2 cs = tb[(size_t)k * D.mpts];
-        const float c = cs.x * m.ct[k] - cs.y * m.st[k];
-        se += m.a[k] * c;
-        sp += m.ax[k] * c;
-        sq += m.ay[k] * c;
+    const int nc = D.ncomp;
+    const unsigned long long pol = l2_keep_policy();
+    for (int k0 = 0; k0 < nc; k0 += MK_BATCH) {
+        float2 cs[MK_BATCH];
+#pragma unroll
+        for (int u = 0; u < MK_BATCH; u++)
+            cs[u] = k0 + u < nc ? ld_keep(tb + (size_t)(k0 + u) * D.mpts, pol) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < MK_BATCH; u++) {
+            if (k0 + u < nc) {
+                const float4 f = m.f[2 * (k0 + u)], g = m.f[2 * (k0 + u) + 1];
+                const float c = cs[u].x * f.x - cs[u].y * f.y;
+                se += g.x * c;
+                sp += g.y * c;
+                sq += g.z * c;
+            }
+        }
     }
     e = r * se;
     p = r * sp;
@@ -279,16 +307,26 @@ __device__ __forceinline__ void maker_increment_tab(const Dev<float> &D, const M
 {
     float sp = 0.0f, sq = 0.0f, sq1 = 0.0f;
     const float2 *tb = D.mtab + pt;
-#pragma unroll 8  // eight table loads in flight per point
-    for (int k = 0; k < D.ncomp; k++) {
-        const float2 cs = tb[(size_t)k * D.mpts];
-        const float c0 = cs.x * m.ct[k] - cs.y * m.st[k];
-        const float s0 = cs.y * m.ct[k] + cs.x * m.st[k];
-        const float term = c0 * (dr + r1 * m.cm1[k]) - r1 * s0 * m.sd[k];
-        const float c1 = c0 + (c0 * m.cm1[k] - s0 * m.sd[k]);
-        sp += m.ax[k] * term;
-        sq += m.ay[k] * term;
-        sq1 += m.ay[k] * c1;
+    const int nc = D.ncomp;
+    const unsigned long long pol = l2_keep_policy();
+    for (int k0 = 0; k0 < nc; k0 += MK_BATCH) {
+        float2 cs[MK_BATCH];
+#pragma unroll
+        for (int u = 0; u < MK_BATCH; u++)
+            cs[u] = k0 + u < nc ? ld_keep(tb + (size_t)(k0 + u) * D.mpts, pol) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < MK_BATCH; u++) {
+            if (k0 + u < nc) {
+                const float4 f = m.f[2 * (k0 + u)], g = m.f[2 * (k0 + u) + 1];
+                const float c0 = cs[u].x * f.x - cs[u].y * f.y;
+                const float s0 = cs[u].y * f.x + cs[u].x * f.y;
+                const float term = c0 * (dr + r1 * f.w) - r1 * s0 * f.z;
+                const float c1 = c0 + (c0 * f.w - s0 * f.z);
+                sp += g.y * term;
+                sq += g.z * term;
+                sq1 += g.z * c1;
+            }
+        }
     }
     dp = sp;
     dq = sq;
@@ -3653,12 +3691,23 @@ static bool rhs_fast(const Dev<T> &D)
     return D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 && (D.kahan != 0) == (sizeof(T) == 4) &&
            D.fstride * 15 < 0x7fffffffLL;
 }
+// Rows per warp of the sliding-window RHS kernels: 64 (the fewest halo rows
+// re-read per strip) unless the grid then has fewer warps than four per
+// multiprocessor (domains of a few million cells or less: 1000 x 1500 has
+// 408 strips of 64 rows), then 32, which doubles them.
+template <typename T>
+static int rhs_rows(const Dev<T> &D)
+{
+    if (D.tune_rows > 0) return D.tune_rows;
+    const long long warps64 = (long long)((D.nx + 59) / 60) * ((D.ny + 63) / 64);  // paired strips
+    return warps64 >= 4LL * D.nsm ? 64 : 32;
+}
 // the paired single-precision RHS kernel: the fast configuration, with or
 // without bottom friction
 template <typename T>
 static bool rhs_pair(const Dev<T> &D)
 {
-    const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
+    const int rows = rhs_rows(D);
     return sizeof(T) == 4 && D.tune_rhs != 1 && D.tune_rhs1 == 0 && rows != 16 && D.theta == (T)1 &&
            D.cross_mode != 0 && D.kahan != 0 && D.fstride * 15 < 0x7fffffffLL;
 }
@@ -3666,7 +3715,7 @@ static bool rhs_pair(const Dev<T> &D)
 template <typename T>
 static bool rhs_fuses_ysum(const Dev<T> &D)
 {
-    const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
+    const int rows = rhs_rows(D);
     return D.tune_rhs != 1 && (rhs_fast(D) || rhs_pair(D)) && D.ysplit && rows != 16 && D.tune_ysum == 0;
 }
 
@@ -3698,7 +3747,7 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         dim3 g1((nx + TX - 1) / TX, (ny + TY - 1) / TY);
         k_rhs_combine<T, TX, TY><<<g1, dim3(TX, TY), 0, st>>>(D);
     } else {
-        const int rows = D.tune_rows > 0 ? D.tune_rows : 64;
+        const int rows = rhs_rows(D);
         const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
         const int nband = (ny + rows - 1) / rows;
         const long long nwarp = (long long)nstrip * nband;
