@@ -94,7 +94,9 @@ typedef struct {
                               with two rows in flight per block, bit 3: persistent x-solver
                               with one row in flight, bit 4: x-solver with one warp per row
                               (the single-precision default); [3] rows per warp
-                              of the sliding window (16, 32, 64); [4] x-solver elements per
+                              of the sliding window (16, 24, 32, 48, 64; 16 selects the
+                              one-column kernel, which takes 24 and 48 as 32; 0: by grid
+                              size); [4] x-solver elements per
                               thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
                               y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
                               of their own instead of inside the RHS kernel, bit 1: one column

@@ -297,7 +297,9 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.tune_ykch = p.tune[0] == 8 || p.tune[0] == 16 || p.tune[0] == 32 ? p.tune[0] : 0;
     D.tune_ythreads = p.tune[1] >= 32 && p.tune[1] <= 512 ? p.tune[1] : 0;
     D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
-    D.tune_rows = p.tune[3] == 16 || p.tune[3] == 32 || p.tune[3] == 64 ? (p.tune[3] & 127) : 0;
+    D.tune_rows = p.tune[3] == 16 || p.tune[3] == 24 || p.tune[3] == 32 || p.tune[3] == 48 || p.tune[3] == 64
+                      ? p.tune[3]
+                      : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
     D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));

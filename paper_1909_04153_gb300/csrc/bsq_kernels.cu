@@ -246,12 +246,14 @@ __device__ MakerStep maker_step(const Dev<T> &D, double t, double t_next)
     return MakerStep{maker_sm};
 }
 
-// The table is read in batches of MK_BATCH components, all loads of a batch
-// issued before their use: a point's sum is a chain of load latencies, one
-// per batch (a handful of points per block, so little else hides them).  The
-// loads carry an L2 evict-last policy, so the table (a few MB, read every
-// step) tends to stay in L2 while the step's streaming kernels pass through.
-constexpr int MK_BATCH = 32;
+// The table is read in batches of MB components, all loads of a batch issued
+// before their use: a point's sum is a chain of load latencies, one per batch
+// (a handful of points per block, so little else hides them).  32 for the
+// single-domain ghost kernels (a few dozen blocks), 16 for the batched one,
+// whose thousand-odd blocks want the registers for residency.  The loads
+// carry an L2 evict-last policy, so the table (a few megabytes, read every step)
+// tends to stay in L2 while the step's streaming kernels pass through.
+constexpr int MK_BATCH_ONE = 32, MK_BATCH_MANY = 16;
 
 __device__ __forceinline__ unsigned long long l2_keep_policy()
 {
@@ -268,6 +270,7 @@ __device__ __forceinline__ float2 ld_keep(const float2 *p, unsigned long long po
 }
 
 // Maker state (eta, P, Q) at maker point pt and the factors' time, ramp r.
+template <int MB>
 __device__ __forceinline__ void maker_state_tab(const Dev<float> &D, const MakerStep &m, int pt, float r, float &e,
                                                 float &p, float &q)
 {
@@ -275,13 +278,13 @@ __device__ __forceinline__ void maker_state_tab(const Dev<float> &D, const Maker
     const float2 *tb = D.mtab + pt;
     const int nc = D.ncomp;
     const unsigned long long pol = l2_keep_policy();
-    for (int k0 = 0; k0 < nc; k0 += MK_BATCH) {
-        float2 cs[MK_BATCH];
+    for (int k0 = 0; k0 < nc; k0 += MB) {
+        float2 cs[MB];
 #pragma unroll
-        for (int u = 0; u < MK_BATCH; u++)
+        for (int u = 0; u < MB; u++)
             cs[u] = k0 + u < nc ? ld_keep(tb + (size_t)(k0 + u) * D.mpts, pol) : make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int u = 0; u < MK_BATCH; u++) {
+        for (int u = 0; u < MB; u++) {
             if (k0 + u < nc) {
                 const float4 f = m.f[2 * (k0 + u)], g = m.f[2 * (k0 + u) + 1];
                 const float c = cs[u].x * f.x - cs[u].y * f.y;
@@ -302,6 +305,7 @@ __device__ __forceinline__ void maker_state_tab(const Dev<float> &D, const Maker
 //   r1 cos(ph0 + d) - r0 cos(ph0) = cos(ph0) ((r1 - r0) + r1 (cos d - 1)) - r1 sin(ph0) sin d
 // so that it keeps single-precision relative accuracy instead of the
 // absolute error of two cosines.
+template <int MB>
 __device__ __forceinline__ void maker_increment_tab(const Dev<float> &D, const MakerStep &m, int pt, float dr,
                                                     float r1, float &dp, float &dq, float &q1)
 {
@@ -309,13 +313,13 @@ __device__ __forceinline__ void maker_increment_tab(const Dev<float> &D, const M
     const float2 *tb = D.mtab + pt;
     const int nc = D.ncomp;
     const unsigned long long pol = l2_keep_policy();
-    for (int k0 = 0; k0 < nc; k0 += MK_BATCH) {
-        float2 cs[MK_BATCH];
+    for (int k0 = 0; k0 < nc; k0 += MB) {
+        float2 cs[MB];
 #pragma unroll
-        for (int u = 0; u < MK_BATCH; u++)
+        for (int u = 0; u < MB; u++)
             cs[u] = k0 + u < nc ? ld_keep(tb + (size_t)(k0 + u) * D.mpts, pol) : make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int u = 0; u < MK_BATCH; u++) {
+        for (int u = 0; u < MB; u++) {
             if (k0 + u < nc) {
                 const float4 f = m.f[2 * (k0 + u)], g = m.f[2 * (k0 + u) + 1];
                 const float c0 = cs[u].x * f.x - cs[u].y * f.y;
@@ -457,7 +461,7 @@ template <> __device__ __forceinline__ double coefv<double>(const Coef &c, int w
 // the filled columns (mirror with Q negated, or the maker).
 // The single-precision path evaluates the maker from the table with the
 // step factors m (filled for time t); the double-precision path directly.
-template <typename T>
+template <typename T, int MB>
 __device__ void ghost_value(const Dev<T> &D, const MakerStep &m, const T *w, int i, int j, double t, double ramp,
                             T &gw, T &gP, T &gQ)
 {
@@ -486,7 +490,7 @@ __device__ void ghost_value(const Dev<T> &D, const MakerStep &m, const T *w, int
         // (Q negated) of the maker column cell (i, sj) it faces
         T e, p, q;
         if constexpr (sizeof(T) == 4) {
-            maker_state_tab(D, m, maker_point(D, side, i, sj), (float)ramp, e, p, q);
+            maker_state_tab<MB>(D, m, maker_point(D, side, i, sj), (float)ramp, e, p, q);
         } else {
             maker_state(D, ((double)i + 0.5) * D.dxd, ((double)sj + 0.5) * D.dyd, t, ramp, e, p, q);
         }
@@ -507,7 +511,7 @@ __device__ void ghost_value(const Dev<T> &D, const MakerStep &m, const T *w, int
 
 // Ghost fill at t_n + maker corrections of the line systems (the controller of
 // this step ran at the end of the previous step, or in the prologue).
-template <typename T>
+template <typename T, int MB>
 __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, long long stride)
 {
     const Coef scf = *D.coef;
@@ -529,7 +533,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
             int g = rem / ny + 1, j = rem - (g - 1) * ny;
             int i = side == 0 ? -g : nx - 1 + g;
             T a, b, c;
-            ghost_value(D, m, w, i, j, t0, r0, a, b, c);
+            ghost_value<T, MB>(D, m, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else if (idx < nghost) {
@@ -539,7 +543,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
             int g = rem / (nx + 4) + 1, i = rem - (g - 1) * (nx + 4) - 2;
             int j = side == 0 ? -g : ny - 1 + g;
             T a, b, c;
-            ghost_value(D, m, w, i, j, t0, r0, a, b, c);
+            ghost_value<T, MB>(D, m, w, i, j, t0, r0, a, b, c);
             long long f = fidx(D, i, j);
             w[f] = a; D.P[f] = b; D.Q[f] = c;
         } else {
@@ -553,7 +557,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                     double dp, dq, q1;
                     if constexpr (sizeof(T) == 4) {
                         float fp, fq, fq1;
-                        maker_increment_tab(D, m, maker_point(D, s, side == 0 ? -1 : nx, j), (float)(r1 - r0),
+                        maker_increment_tab<MB>(D, m, maker_point(D, s, side == 0 ? -1 : nx, j), (float)(r1 - r0),
                                             (float)r1, fp, fq, fq1);
                         dp = fp; dq = fq; q1 = fq1;
                     } else {
@@ -578,7 +582,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                     double dp, dq, q1;
                     if constexpr (sizeof(T) == 4) {
                         float fp, fq, fq1;
-                        maker_increment_tab(D, m, maker_point(D, s, i, jg), (float)(r1 - r0), (float)r1, fp, fq, fq1);
+                        maker_increment_tab<MB>(D, m, maker_point(D, s, i, jg), (float)(r1 - r0), (float)r1, fp, fq, fq1);
                         dp = fp; dq = fq; q1 = fq1;
                     } else {
                         maker_increment(D, x, y, t0, t1, r0, r1, dp, dq, q1);
@@ -591,7 +595,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
                         const int ic = i == 0 ? -1 : nx;
                         if constexpr (sizeof(T) == 4) {
                             float fp, fq, fq1;
-                            maker_increment_tab(D, m, maker_point(D, s, ic, jg), (float)(r1 - r0), (float)r1, fp, fq,
+                            maker_increment_tab<MB>(D, m, maker_point(D, s, ic, jg), (float)(r1 - r0), (float)r1, fp, fq,
                                                 fq1);
                             q1 = fq1;
                         } else {
@@ -610,7 +614,7 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
 template <typename T>
 __global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
 {
-    ghost_body(D, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    ghost_body<T, MK_BATCH_ONE>(D, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 // Ghost layers of Q at t_{n+1} (after the y-line solves), for F*(Q^{n+1}).
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(256) k_ghost_q(Dev<T> D)
             j = side == 0 ? -g : ny - 1 + g;
         }
         T a, b, c;
-        ghost_value(D, m, w, i, j, cf.t1, cf.ramp1, a, b, c);
+        ghost_value<T, MK_BATCH_ONE>(D, m, w, i, j, cf.t1, cf.ramp1, a, b, c);
         D.Q[fidx(D, i, j)] = c;
     }
 }
@@ -3691,32 +3695,54 @@ static bool rhs_fast(const Dev<T> &D)
     return D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 && (D.kahan != 0) == (sizeof(T) == 4) &&
            D.fstride * 15 < 0x7fffffffLL;
 }
-// Rows per warp of the sliding-window RHS kernels: 64 (the fewest halo rows
-// re-read per strip) unless the grid then has fewer warps than four per
-// multiprocessor (domains of a few million cells or less: 1000 x 1500 has
-// 408 strips of 64 rows), then 32, which doubles them.
-template <typename T>
-static int rhs_rows(const Dev<T> &D)
-{
-    if (D.tune_rows > 0) return D.tune_rows;
-    const long long warps64 = (long long)((D.nx + 59) / 60) * ((D.ny + 63) / 64);  // paired strips
-    return warps64 >= 4LL * D.nsm ? 64 : 32;
-}
 // the paired single-precision RHS kernel: the fast configuration, with or
-// without bottom friction
+// without bottom friction (tune_rows 16 asks for the one-column kernel)
 template <typename T>
 static bool rhs_pair(const Dev<T> &D)
 {
-    const int rows = rhs_rows(D);
-    return sizeof(T) == 4 && D.tune_rhs != 1 && D.tune_rhs1 == 0 && rows != 16 && D.theta == (T)1 &&
+    return sizeof(T) == 4 && D.tune_rhs != 1 && D.tune_rhs1 == 0 && D.tune_rows != 16 && D.theta == (T)1 &&
            D.cross_mode != 0 && D.kahan != 0 && D.fstride * 15 < 0x7fffffffLL;
+}
+// Rows per warp of the sliding-window RHS kernels.  A warp walks its strip's
+// rows plus 4 halo rows, and two blocks of four warps fit a multiprocessor, so
+// a launch takes about waves x (rows + 4) row steps, waves = blocks / (2 x
+// multiprocessors) rounded up.  Where 64-row strips fill the device (at least
+// one wave: 2048 x 2048 and up) the paired kernel takes 64; on smaller grids
+// the multiple of the y-chunk rows in {64, 48, 32, 24, 16} that minimises the
+// estimate (24 at 1000 x 1500, 16 below a million cells).  The one-column
+// kernels are compiled for 16, 32 and 64 rows and take 64, or 32 when 64-row
+// strips give fewer than four warps per multiprocessor.
+template <typename T>
+static int rhs_rows(const Dev<T> &D)
+{
+    const bool pair = rhs_pair(D);
+    if (D.tune_rows > 0) return pair || D.tune_rows == 16 || D.tune_rows == 64 ? D.tune_rows : 32;
+    if (!pair) {
+        const long long warps64 = (long long)((D.nx + SW_COLS - 1) / SW_COLS) * ((D.ny + 63) / 64);
+        return warps64 >= 4LL * D.nsm ? 64 : 32;
+    }
+    const int ky = ysplit_rows<T>(D.tune_yk);
+    const long long nstrip = (D.nx + SW2_COLS - 1) / SW2_COLS, slots = 8LL * D.nsm;
+    if (nstrip * ((D.ny + 63) / 64) >= slots) return 64;
+    const int cand[5] = {64, 48, 32, 24, 16};
+    int best = 64;
+    long long best_cost = -1;
+    for (int q = 0; q < 5; q++) {
+        const int r = cand[q];
+        if (r % ky) continue;
+        const long long warps = nstrip * ((D.ny + r - 1) / r);
+        const long long cost = ((warps + slots - 1) / slots) * (r + 4);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = r; }
+    }
+    return best;
 }
 // 1 when the RHS kernel forms the y-line chunk summaries (no k_ysum launch)
 template <typename T>
 static bool rhs_fuses_ysum(const Dev<T> &D)
 {
     const int rows = rhs_rows(D);
-    return D.tune_rhs != 1 && (rhs_fast(D) || rhs_pair(D)) && D.ysplit && rows != 16 && D.tune_ysum == 0;
+    const bool pair_fuses = rhs_pair(D) && rows % ysplit_rows<T>(D.tune_yk) == 0;  // bands start on chunks
+    return D.tune_rhs != 1 && (pair_fuses || (rhs_fast(D) && rows != 16)) && D.ysplit && D.tune_ysum == 0;
 }
 
 // Dynamic shared memory of the ghost kernels: the single-precision maker's
@@ -3951,7 +3977,7 @@ __global__ void __launch_bounds__(256) k_ghost_b(const Dev<T> *Ds, const int4 *t
 {
     const int4 e = tab[blockIdx.x];
     const Dev<T> &D = batch_dev(Ds, e.x);
-    ghost_body(D, (long long)e.y * blockDim.x + threadIdx.x, (long long)e.z * blockDim.x);
+    ghost_body<T, MK_BATCH_MANY>(D, (long long)e.y * blockDim.x + threadIdx.x, (long long)e.z * blockDim.x);
 }
 
 // table entry: (domain, block of that domain, strips of 28 columns, 0)

@@ -264,7 +264,8 @@ def test_bounded_wait_times_out():
 @pytest.mark.parametrize("tune", [(0, 0, 1, 0), (0, 0, 2, 0), (0, 0, 3, 0), (8, 256, 0, 16), (32, 512, 0, 64),
                                   (0, 0, 8, 0, 4), (0, 0, 8, 0, 8), (0, 0, 0, 0, 4),
                                   (0, 0, 16, 0, 4), (0, 0, 16, 0, 8), (0, 0, 0, 0, 0, 0, 1), (0, 0, 0, 32, 0, 16),
-                                  (0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 32, 0, 0, 3), (0, 0, 4, 0, 4), (0, 0, 4, 0, 8)])
+                                  (0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 32, 0, 0, 3), (0, 0, 4, 0, 4), (0, 0, 4, 0, 8),
+                                  (0, 0, 0, 24), (0, 0, 0, 48), (0, 0, 0, 24, 0, 16), (0, 0, 0, 64)])
 def test_kernel_variants_match_oracle(tune):
     # every kernel shape (tiled or sliding-window RHS, TMA-staged or register
     # x-solver, y-solver chunk sizes) gives the same step to FP64 round-off
