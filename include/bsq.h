@@ -189,6 +189,12 @@ size_t bsq_device_bytes(const bsq_domain *d);
 bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels);
 const char *bsq_kernel_name(int k);
 
+/* Measured FP64 fused multiply-add rate of the current device (TFLOP/s, 2
+ * flops per FMA) from a short kernel of independent FMA chains (about 1 ms);
+ * the roof for the double-precision path, which on this device is bound by
+ * FP64 arithmetic, not memory.  Errors: BSQ_ERR_ARG, BSQ_ERR_CUDA. */
+bsq_status bsq_fp64_fma_rate(double *tflops);
+
 /* Kernel launches one step makes (each a node of the captured graphs);
  * 0 for a NULL handle. */
 int bsq_launches_per_step(const bsq_domain *d);

@@ -103,6 +103,8 @@ def lib():
         L.bsq_kernel_name.argtypes = [ctypes.c_int]
         L.bsq_launches_per_step.restype = ctypes.c_int
         L.bsq_launches_per_step.argtypes = [vp]
+        L.bsq_fp64_fma_rate.restype = ctypes.c_int
+        L.bsq_fp64_fma_rate.argtypes = [_DP]
         L.bsq_batch_create.restype = ctypes.c_int
         L.bsq_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.bsq_batch_advance.restype = ctypes.c_int
@@ -452,6 +454,15 @@ def bsq_clock(h) -> tuple:
     t, n = ctypes.c_double(), ctypes.c_longlong()
     st = lib().bsq_clock(h, ctypes.byref(t), ctypes.byref(n))
     return t.value, n.value, st
+
+
+def fp64_fma_rate() -> float:
+    """Measured FP64 FMA rate of the current device, TFLOP/s (bsq_fp64_fma_rate)."""
+    v = ctypes.c_double()
+    st = lib().bsq_fp64_fma_rate(ctypes.byref(v))
+    if st != OK:
+        raise BsqError(st, "bsq_fp64_fma_rate")
+    return v.value
 
 
 def bsq_domain_bytes(params: bsq_params, n_comp: int = 0) -> int:

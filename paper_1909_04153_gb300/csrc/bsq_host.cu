@@ -1220,6 +1220,38 @@ extern "C" const char *bsq_kernel_name(int k)
     return (k >= 0 && k < 5) ? kKernelNames[k] : "";
 }
 
+extern "C" bsq_status bsq_fp64_fma_rate(double *tflops)
+{
+    if (!tflops) return BSQ_ERR_ARG;
+    *tflops = 0.0;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return BSQ_ERR_CUDA;
+    const int blocks = 8 * nsm, n = 2048;  // 8 blocks of 256 threads a multiprocessor
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double *out = nullptr;
+    bsq_status rc = BSQ_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+        cudaMalloc((void **)&out, (size_t)blocks * 256 * sizeof(double)) == cudaSuccess &&
+        launch_fma64(out, blocks, n, st) == cudaSuccess &&  // warm-up
+        cudaEventRecord(e0, st) == cudaSuccess && launch_fma64(out, blocks, n, st) == cudaSuccess &&
+        cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f) {
+            *tflops = 2.0 * 8.0 * n * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+            rc = BSQ_OK;
+        }
+    }
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
 extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, double *ms_out, int *n_kernels)
 {
     if (!d || !ms_out || !n_kernels || n_steps <= 0) return BSQ_ERR_ARG;

@@ -1391,8 +1391,9 @@ __device__ __forceinline__ void flux_pair(const FS2 &L, const FS2 &R, float g, f
 
 constexpr int SW2_COLS = 60;  // interior columns per warp strip (two per lane, lanes 1..30)
 
-// FRIC: quadratic bottom friction f1 = f u |u|, f2 = f v |u| (desingularised
-// centre velocities, SURVEY reading A10) in F and G
+// FRIC: quadratic bottom friction f1 = f u |u|, f2 = f v |u| in F and G, with
+// the desingularised centre velocities (the paper names the quadratic law and
+// f = 0.0025 in Sec. 5.4 without writing it out)
 template <int YS, bool FRIC = false>
 __device__ __forceinline__ void rhs_sw2_body(const Dev<float> &D, int blk, int nstrip, int ROWS)
 {
@@ -3471,6 +3472,30 @@ cudaError_t launch_maker_table(const Dev<T> &D, cudaStream_t st)
 }
 
 // ------------------------------------------------------------------ utilities
+
+// FP64 fused multiply-add throughput: each thread runs 8 independent chains
+// x <- x a + b of n steps (|a| < 1 keeps the values bounded) and stores their
+// sum, which keeps every chain live.
+__global__ void __launch_bounds__(256) k_fma64(double *out, int n, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) x[q] = (double)(threadIdx.x + q) * 1e-3;
+    for (int i = 0; i < n; i++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) x[q] = fma(x[q], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += x[q];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma64(double *out, int blocks, int n, cudaStream_t st)
+{
+    k_fma64<<<blocks, 256, 0, st>>>(out, n, 0.999, 1e-3);
+    return cudaGetLastError();
+}
 
 // Eq. 22 rate of the current state (used at creation and after a restore).
 template <typename T>

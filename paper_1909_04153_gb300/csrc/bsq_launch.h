@@ -24,6 +24,7 @@ template <typename T> cudaError_t launch_maker_table(const Dev<T> &D, cudaStream
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
 template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);
 cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long max_steps);
+cudaError_t launch_fma64(double *out, int blocks, int n, cudaStream_t st);  // 256 threads a block
 
 // batched steps over many domains (one launch per stage)
 template <typename T> int batch_xchunk();

@@ -279,3 +279,10 @@ def test_kernel_variants_match_oracle(tune):
     with bsq.Domain(case, precision="fp32", tune=tune) as d:
         d.step_dt(dts)
         assert rel(d.read("eta"), o.get("eta")) <= FP32_TOL, tune
+
+
+def test_fp64_fma_rate_is_measured():
+    # the FP64 roof of the double-precision path: a positive, finite rate
+    # below the FP32 rate's order of magnitude
+    r = bsq.fp64_fma_rate()
+    assert 0.05 < r < 100.0, r
