@@ -399,3 +399,25 @@ def test_sine_maker_generates_the_model_wavelength():
     assert abs(k_fit - k) / k < 0.02, (k_fit, k)
     amp = 0.5 * (seg.max() - seg.min())
     assert 0.8 * H / 2 < amp < 1.2 * H / 2, amp
+
+
+def test_oblique_maker_state_closed_form():
+    # One linear component travelling at angle theta (A20): eta = r(t) a cos(k (x cos theta +
+    # y sin theta) - omega t + phi), P and Q = (omega / k) (cos theta, sin theta) eta, k from
+    # the Madsen-Sorensen dispersion relation at the maker's still depth, r = tanh(3 t / ramp).
+    # A swapped cos/sin, a dropped sign or a missing ramp fails one of the sampled points.
+    depth, T, a, phi, theta, ramp = 0.6, 1.4, 0.004, 0.7, 0.4, 2.0
+    om = 2 * math.pi / T
+    k = brentq(lambda k: G * depth * k * k * (1 + B15 * (k * depth) ** 2) / (1 + (B15 + 1 / 3) * (k * depth) ** 2) - om * om, 1e-6, 100)
+    nx, ny, dx = 40, 30, 0.05
+    bed = np.full((ny + 1, nx + 1), -depth)
+    prm = W.base_params(nx, ny, dx, bc=(2, 0, 0, 0), ramp_time=ramp)
+    D = oracle.OracleDomain(prm, bed, np.array([[a, 1 / T, phi, theta]]), None, None, None)
+    assert abs(D.component_k(0) - k) < 1e-10 * k
+    c = om / k
+    for x, y, t in [(-0.025, 0.3, 0.1), (-0.075, 1.2, 0.9), (-0.025, -0.025, 3.3), (0.4, 0.7, 5.0)]:
+        r = math.tanh(3 * t / ramp)
+        eta = r * a * math.cos(k * (x * math.cos(theta) + y * math.sin(theta)) - om * t + phi)
+        got = D.maker_state(x, y, t)
+        np.testing.assert_allclose(got, [eta, c * math.cos(theta) * eta, c * math.sin(theta) * eta],
+                                   rtol=1e-12, atol=1e-16)
