@@ -215,10 +215,11 @@ __device__ __forceinline__ int maker_point(const Dev<T> &D, int side, int i, int
 }
 
 // Per-component factors of one step: cos and sin of -omega t, sin d and
-// cos d - 1 of d = -omega (t_next - t) from their Taylor series (|d| is a
-// small fraction of a radian at any stable step), and a, a cx, a cy; two
-// float4 per component, f[2k] = (cos, sin, sin d, cos d - 1) and
-// f[2k + 1] = (a, a cx, a cy, 0).
+// cos d - 1 of d = -omega (t_next - t), and a, a cx, a cy; two float4 per
+// component, f[2k] = (cos, sin, sin d, cos d - 1) and f[2k + 1] =
+// (a, a cx, a cy, 0).  For |d| <= 1/4 (a step below a 25th of the period, the
+// usual case) sin d and cos d - 1 come from their Taylor series, truncated
+// below 1e-8 relative; larger steps take sin d and -2 sin^2(d/2) in FP64.
 struct MakerStep {
     const float4 *f;
 };
@@ -235,9 +236,17 @@ __device__ MakerStep maker_step(const Dev<T> &D, double t, double t_next)
     for (int k = threadIdx.x; k < D.ncomp; k += blockDim.x) {
         float s, c;
         sincos_phase_f(-D.om[k] * t, s, c);
-        const float d = (float)(-D.om[k] * (t_next - t)), d2 = d * d;
-        const float sd = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-        const float cm1 = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+        const double dd = -D.om[k] * (t_next - t);
+        float sd, cm1;
+        if (fabs(dd) <= 0.25) {
+            const float d = (float)dd, d2 = d * d;
+            sd = d * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
+            cm1 = -d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+        } else {
+            const double sh = sin(0.5 * dd);
+            sd = (float)sin(dd);
+            cm1 = (float)(-2.0 * sh * sh);
+        }
         const float ak = (float)D.amp[k];
         maker_sm[2 * k] = make_float4(c, s, sd, cm1);
         maker_sm[2 * k + 1] = make_float4(ak, (float)D.cx[k] * ak, (float)D.cy[k] * ak, 0.0f);

@@ -286,3 +286,26 @@ def test_fp64_fma_rate_is_measured():
     # below the FP32 rate's order of magnitude
     r = bsq.fp64_fma_rate()
     assert 0.05 < r < 100.0, r
+
+
+def test_fp32_maker_with_steps_above_a_25th_of_the_period():
+    # fixed steps of 0.19-0.33 rad per step for the maker components: above
+    # 1/4 rad the single-precision maker takes sin d and cos d - 1 in FP64
+    # instead of their Taylor series; both branches run here
+    nx, ny, dx, h = 48, 16, 0.5, 0.4
+    bed = np.full((ny + 1, nx + 1), -h)
+    comps = W.jonswap_components(0.05, 0.8, n=16, f0=1.0, df=0.05, seed=5)
+    comps[:, 3] = np.random.default_rng(6).uniform(-0.5, 0.5, size=16)
+    dt = 0.12 * dx / np.sqrt(W.G * h)
+    od = 2 * np.pi * comps[:, 1] * dt
+    assert (od > 0.25).any() and (od <= 0.25).any()
+    prm = W.base_params(nx, ny, dx, bc=(W.MAKER, W.SPONGE, W.WALL, W.WALL), sponge_width=(0, 6.0, 0, 0),
+                        ramp_time=2.0, cfl=0.0, dt_init=dt)
+    case = dict(params=prm, bed=bed, comps=comps, eta0=None, P0=None, Q0=None)
+    steps = 400
+    o = _oracle(case)
+    o.run(steps, dts=[dt] * steps)
+    with bsq.Domain(case, precision="fp32") as d:
+        assert d.advance(t_end=dt * steps) == steps
+        # FP32 resolves eta to ~1e-7 of the depth; the waves here are ~6e-4 m rms
+        assert rel(d.read("eta"), o.get("eta")) <= 1e-3
