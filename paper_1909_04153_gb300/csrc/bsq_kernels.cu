@@ -3079,12 +3079,15 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_grp(Dev<T> D, int span, doubl
 // and finishes each chunk at once: compensated P update, sponge on w and P,
 // Eq. 22 rate.  Warps never wait on each other, so every row of the grid can
 // be in flight at once.  Same arithmetic as k_xsolve.
-template <typename T, int K>
+// FIXED: the default configuration (sequential cross form, compensated
+// accumulation) compiled in, no run-time switches on either
+template <typename T, int K, bool FIXED = false>
 __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf, int j, T *ys, T &rate, bool &bad)
 {
     const int lane = threadIdx.x & 31;
     const int nx = D.nx, ny = D.ny;
-    const bool seq = D.cross_mode != 0;
+    const bool seq = FIXED || D.cross_mode != 0;
+    const bool kah = FIXED || D.kahan != 0;
     const long long rowo = fidx(D, 0, j);
     const T *Qr = D.Q + rowo, *br = D.bC + rowo;
     const T corrW = D.corrW[j], corrE = D.corrE[j];
@@ -3185,7 +3188,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
         vload_k_if<T, K>(act, D.gx + ib, gxv);
         vload_k_if<T, K>(act, D.fxc + rowo + ib, c);
         vload_k_if<T, K>(act, Pr + ib, Pv);
-        vload_k_if<T, K>(act && D.kahan, cPr + ib, cPv);
+        vload_k_if<T, K>(act && kah, cPr + ib, cPv);
         vload_k_if<T, K>(act, wrow + ib, wv);
         vload_k_if<T, K>(act, Qr + ib, Qv);
         vload_k_if<T, K>(act, br + ib, bv);
@@ -3212,7 +3215,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             const int i = ib + q;
             if (i >= nx) continue;
             T Pn, cn = (T)0;
-            if (D.kahan) {
+            if (kah) {
                 T yy = x[q] - cPv[q];
                 Pn = Pv[q] + yy;
                 cn = (Pn - Pv[q]) - yy;
@@ -3225,7 +3228,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
                 T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
                 wq = bv[q] + (d + gm * (h - d));
                 wrow[i] = wq;
-                if (D.kahan) cwr[i] = (T)0;
+                if (kah) cwr[i] = (T)0;
                 Pn *= gm;
                 cn *= gm;
             }
@@ -3240,7 +3243,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
         }
         if (ib < nx) {
             vstore_k<T, K>(Pr + ib, Pv);
-            if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
+            if (kah) vstore_k<T, K>(cPr + ib, cPv);
         }
     }
 }
@@ -3257,7 +3260,7 @@ static size_t xwarp_smem(int nx)
 
 // rows blk * XW_WARPS + warp of one domain; the controller of the domain's
 // next step runs in the last of its nparts blocks
-template <typename T, int K>
+template <typename T, int K, bool FIXED = false>
 __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsigned nparts, int yrow,
                                                  double forced_dt_next)
 {
@@ -3270,7 +3273,7 @@ __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsig
     const int j = blk * XW_WARPS + wid;
     T rate = (T)0;
     bool bad = false;
-    if (j < D.ny) xsolve_row_warp<T, K>(D, cf, j, ys, rate, bad);
+    if (j < D.ny) xsolve_row_warp<T, K, FIXED>(D, cf, j, ys, rate, bad);
     double rr = (double)rate;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
@@ -3290,10 +3293,10 @@ __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsig
     }
 }
 
-template <typename T, int K>
+template <typename T, int K, bool FIXED = false>
 __global__ void __launch_bounds__(32 * XW_WARPS, sizeof(T) == 4 ? 4 : 2) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
 {
-    xsolve_warp_body<T, K>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
+    xsolve_warp_body<T, K, FIXED>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
 }
 
 // shared memory bytes of the TMA x-solver for a row span
@@ -3672,6 +3675,10 @@ cudaError_t configure(int nx)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_warp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_warp<T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_xsolve_warp<T, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_warp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     return e;
 }
@@ -3882,12 +3889,15 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     if (ev) cudaEventRecord(ev[4], st);
     if (xwarp) {
         const int xb = (ny + XW_WARPS - 1) / XW_WARPS;
+        const bool fixed = D.cross_mode != 0 && D.kahan != 0;
         if (K == 4) {
             const int yrow = (nx + 127) / 128 * 128;
-            k_xsolve_warp<T, 4><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
+            if (fixed) k_xsolve_warp<T, 4, true><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
+            else k_xsolve_warp<T, 4><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
         } else {
             const int yrow = (nx + 255) / 256 * 256;
-            k_xsolve_warp<T, 8><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
+            if (fixed) k_xsolve_warp<T, 8, true><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
+            else k_xsolve_warp<T, 8><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
         }
     } else if (grp) {
         const int grid = min((ny + 1) / 2, D.nsm);
@@ -4098,7 +4108,7 @@ template <int K>
 __global__ void __launch_bounds__(32 * XW_WARPS, 4) k_xsolve_warp_g(const __grid_constant__ RhsGroup G, const int4 *tab)
 {
     const int4 e = tab[blockIdx.x];
-    xsolve_warp_body<float, K>(G.d[e.x], e.y, (unsigned)e.z, e.w, 0.0);
+    xsolve_warp_body<float, K, true>(G.d[e.x], e.y, (unsigned)e.z, e.w, 0.0);  // paired batches: Kahan, sequential
 }
 
 template <typename T>
