@@ -61,3 +61,19 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1, r.stdout
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_workload_grids():
+    # the timed workloads and their grids: barred beach n x n, planar beach
+    # n x n/4, rip-channel beach n x 3n/2 (1000 x 1500: the 0.02 m cells of Eq. 48's basin)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.case_dims("barred_beach", 2048) == (2048, 2048)
+    assert bench.case_dims("planar_beach", 1024) == (1024, 256)
+    assert bench.case_dims("hamm_rip", 1000) == (1000, 1500)
+    c = bench.make_case("hamm_rip", 100)
+    p = c["params"]
+    assert (p["nx"], p["ny"]) == (100, 150)
+    assert abs(p["dx"] - 0.2) < 1e-12 and abs(p["dy"] - 0.2) < 1e-12
+    assert c["comps"].shape == (68, 4) and p["friction"] == 0.0025
