@@ -72,6 +72,9 @@ def lib():
             L.orc_get.restype = ctypes.c_int
             L.orc_get.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
             L.orc_set_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
+            L.orc_get_padded.restype = ctypes.c_int
+            L.orc_get_padded.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+            L.orc_fill_ghosts.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.orc_info.argtypes = [ctypes.c_void_p, _D, ctypes.POINTER(ctypes.c_longlong), _D, _D, _D,
                                    ctypes.POINTER(ctypes.c_longlong)]
             L.orc_rhs.argtypes = [ctypes.c_void_p, _D, _D, _D, _D, _D, _D]
@@ -225,6 +228,18 @@ class OracleDomain:
     def get(self, field: str) -> np.ndarray:
         out = np.zeros((self.ny, self.nx))
         rc = lib().orc_get(self._h, self.FIELDS[field], _ptr(out))
+        if rc:
+            raise ValueError(field)
+        return out
+
+    def fill_ghosts(self, t: float):
+        """Fill the two ghost layers for time t (Sec. 3.3)."""
+        lib().orc_fill_ghosts(self._h, float(t))
+
+    def get_padded(self, field: str) -> np.ndarray:
+        """w, P or Q with the ghost layers, shape (ny+4, nx+4); cell (i, j) at [j+2, i+2]."""
+        out = np.zeros((self.ny + 4, self.nx + 4))
+        rc = lib().orc_get_padded(self._h, {"w": 0, "P": 1, "Q": 2}[field], _ptr(out))
         if rc:
             raise ValueError(field)
         return out

@@ -858,6 +858,16 @@ int orc_get(const orc_dom *D, int field, double *out)
     return ORC_OK;
 }
 
+/* The raw state w, P or Q (field 0, 1, 2) with its two ghost layers,
+ * (nx+4)*(ny+4) values, x fastest, cell (i, j) at (i+2) + (j+2)(nx+4). */
+int orc_get_padded(const orc_dom *D, int field, double *out)
+{
+    const double *src = field == 0 ? D->w : field == 1 ? D->P : field == 2 ? D->Q : NULL;
+    if (!src) return ORC_ERR_ARG;
+    for (int k = 0; k < D->sx * D->sy; k++) out[k] = src[k];
+    return ORC_OK;
+}
+
 /* Overwrite the interior state from eta, P, Q (nx*ny each, NULL keeps). */
 int orc_set_state(orc_dom *D, const double *eta, const double *P, const double *Q)
 {

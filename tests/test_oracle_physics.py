@@ -421,3 +421,33 @@ def test_oblique_maker_state_closed_form():
         got = D.maker_state(x, y, t)
         np.testing.assert_allclose(got, [eta, c * math.cos(theta) * eta, c * math.sin(theta) * eta],
                                    rtol=1e-12, atol=1e-16)
+
+
+def test_ghost_corners_follow_the_column_then_row_fill():
+    # Reading R6 (Sec. 3.3 is silent on the 2x2 corner blocks): the W/E ghost columns
+    # are filled first, then the S/N ghost rows over all columns from the filled
+    # columns (Q negated) or, on a maker side, from the maker.  Oblique components
+    # make the maker vary along y, so evaluating it at the corner itself would differ.
+    nx, ny, dx, t = 20, 16, 0.1, 1.3
+    bed = np.full((ny + 1, nx + 1), -0.5)
+    comps = np.array([[0.01, 0.8, 0.3, 0.5], [0.006, 1.1, 1.7, -0.4]])
+    # maker W, wall S, sponge N: corners take the mirrored maker column
+    D = oracle.OracleDomain(W.base_params(nx, ny, dx, bc=(2, 0, 0, 1), sponge_width=(0, 0, 0, 0.5)),
+                            bed, comps, None, None, None)
+    D.fill_ghosts(t)
+    w, P, Q = (D.get_padded(f) for f in ("w", "P", "Q"))
+    for gi in (-1, -2):
+        for gj, sj in ((-1, 0), (-2, 1), (ny, ny - 1), (ny + 1, ny - 2)):
+            c, s = (gj + 2, gi + 2), (sj + 2, gi + 2)
+            assert w[c] == w[s] and P[c] == P[s] and Q[c] == -Q[s]
+            e, p, q = D.maker_state((gi + 0.5) * dx, (sj + 0.5) * dx, t)
+            assert abs(P[s] - p) <= 1e-15 and abs(Q[s] - q) <= 1e-15
+        assert abs(Q[(2, gi + 2)]) > 1e-6  # the oblique maker has a y flux to negate
+    # maker S, wall W: the S row's corner cells are maker cells at their own position
+    D = oracle.OracleDomain(W.base_params(nx, ny, dx, bc=(0, 0, 2, 0)), bed, comps, None, None, None)
+    D.fill_ghosts(t)
+    P, Q = D.get_padded("P"), D.get_padded("Q")
+    for gi in (-1, -2, nx, nx + 1):
+        for gj in (-1, -2):
+            e, p, q = D.maker_state((gi + 0.5) * dx, (gj + 0.5) * dx, t)
+            assert abs(P[gj + 2, gi + 2] - p) <= 1e-15 and abs(Q[gj + 2, gi + 2] - q) <= 1e-15
