@@ -157,7 +157,7 @@ class OracleDomain:
     ``eta0``, ``P0``, ``Q0``: (ny, nx) initial state or None.
     """
 
-    FIELDS = {"eta": 0, "P": 1, "Q": 2, "h": 3, "w": 4, "b": 5, "d": 6}
+    FIELDS = {"eta": 0, "P": 1, "Q": 2, "h": 3, "w": 4, "b": 5, "d": 6, "sponge": 7}
 
     def __init__(self, params, bed, comps=None, eta0=None, P0=None, Q0=None):
         q = dict(DEFAULTS)

@@ -836,7 +836,8 @@ int orc_step(orc_dom *D, double dt_replay, double t_end)
 /* ------------------------------------------------------------------ */
 /* accessors                                                            */
 
-/* field: 0 eta (= h - d), 1 P, 2 Q, 3 h, 4 w, 5 b (centre), 6 d */
+/* field: 0 eta (= h - d), 1 P, 2 Q, 3 h, 4 w, 5 b (centre), 6 d,
+ * 7 the per-cell sponge factor gamma (1 outside every band) */
 int orc_get(const orc_dom *D, int field, double *out)
 {
     for (int j = 0; j < D->ny; j++)
@@ -851,6 +852,7 @@ int orc_get(const orc_dom *D, int field, double *out)
             case 4: v = D->w[c]; break;
             case 5: v = D->b[c]; break;
             case 6: v = D->d[c]; break;
+            case 7: v = D->sponge[c]; break;
             default: return ORC_ERR_ARG;
             }
             out[i + j * D->nx] = v;

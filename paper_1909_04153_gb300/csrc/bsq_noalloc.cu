@@ -84,6 +84,7 @@ extern "C" bsq_status bsq_mass_noalloc(int precision, const void *w_dev, const v
         return BSQ_ERR_ARG;
     if (precision != BSQ_FP32 && precision != BSQ_FP64) return BSQ_ERR_ARG;
     if (ny > BSQ_NOALLOC_MAX_ROWS) return BSQ_ERR_ARG;  // more rows than the static array holds
+    cudaGetLastError();  // an earlier failed launch elsewhere must not be reported as this call's
     double *rows = nullptr;
     bsq_status st = row_sums_address(&rows);
     if (st != BSQ_OK) return st;

@@ -451,3 +451,107 @@ def test_ghost_corners_follow_the_column_then_row_fill():
         for gj in (-1, -2):
             e, p, q = D.maker_state((gi + 0.5) * dx, (gj + 0.5) * dx, t)
             assert abs(P[gj + 2, gi + 2] - p) <= 1e-15 and abs(Q[gj + 2, gi + 2] - q) <= 1e-15
+
+
+# ------------------------------------------------------------------ sponge layers (Sec. 3.3, reading A19)
+
+def test_sponge_profile_at_the_wall_middle_and_inner_edge():
+    # Reading A19: inside a band of width L the factor rises smoothly from 0 at
+    # the outer wall to 1 at the band's inner edge, passes 1/2 half-way, is 1
+    # beyond the band, and a corner takes the product of its two sides.  The
+    # band widths put a cell centre exactly half-way into each band.
+    nx, ny, dx = 40, 30, 0.1
+    Lw, Le, Ls, Ln = 0.9, 0.5, 0.7, 1.1   # 2 (k + 1/2) dx: cell k centred at L/2
+    bed = np.full((ny + 1, nx + 1), -0.5)
+    D = oracle.OracleDomain(W.base_params(nx, ny, dx, bc=(1, 1, 1, 1), sponge_width=(Lw, Le, Ls, Ln)),
+                            bed, None, None, None, None)
+    g = D.get("sponge")
+    assert np.all(g >= 0.0) and np.all(g <= 1.0)
+    jm, im = ny // 2, nx // 2
+    row, col = g[jm], g[:, im]  # away from the S/N bands, away from the W/E bands
+    # half-way into each band
+    assert abs(row[4] - 0.5) < 1e-14 and abs(row[nx - 1 - 2] - 0.5) < 1e-14
+    assert abs(col[3] - 0.5) < 1e-14 and abs(col[ny - 1 - 5] - 0.5) < 1e-14
+    # nearly zero at the wall: the first cell centre sits dx/2 from it, where a
+    # profile with zero value and zero slope at the wall is of order (dx/L)^2
+    for v, L in ((row[0], Lw), (row[-1], Le), (col[0], Ls), (col[-1], Ln)):
+        assert 0.0 < v < (dx / L) ** 2, (v, L)
+    # rising from the wall to the inner edge, then exactly 1 outside the bands
+    nw, ne = int(round(Lw / dx)), int(round(Le / dx))
+    assert np.all(np.diff(row[:nw]) > 0) and np.all(np.diff(row[nx - ne:]) < 0)
+    assert np.all(row[nw:nx - ne] == 1.0) and np.all(col[int(round(Ls / dx)):ny - int(round(Ln / dx))] == 1.0)
+    # near the inner edge the factor is 1 - O(((L - r)/L)^2): a smooth join
+    assert 1.0 - row[nw - 1] < (dx / Lw) ** 2 * 3
+    # corners: product of the two sides' factors
+    np.testing.assert_allclose(g[0, 0], row[0] * col[0], rtol=1e-14)
+    np.testing.assert_allclose(g[-1, -1], row[-1] * col[-1], rtol=1e-14)
+    np.testing.assert_allclose(g[3, nx - 3], row[nx - 3] * col[3], rtol=1e-14)
+
+
+def _channel_eta(nx, east_bc, sponge_len, dx, depth, T, H, t_end, dt):
+    ny = 3
+    bed = np.full((ny + 1, nx + 1), -depth)
+    prm = W.base_params(nx, ny, dx, bc=(2, east_bc, 0, 0), sponge_width=(0, sponge_len, 0, 0),
+                        ramp_time=3 * T)
+    D = oracle.OracleDomain(prm, bed, np.array([[H / 2, 1 / T, 0.0, 0.0]]), None, None, None)
+    D.run(0, dts=[dt] * int(round(t_end / dt)))  # the same fixed steps in every channel
+    return D.get("eta")[1]
+
+
+def test_sponge_absorbs_what_a_wall_reflects():
+    # Regular waves from the west run down a 1D channel.  A long channel, whose
+    # far end the waves cannot reach and return from in time, gives the
+    # incident wave alone.  In a short channel the wave reaches the east end and
+    # comes back over the probe zone near the maker: a wall sends back all of
+    # it (a standing wave, difference from the incident wave of the order of the
+    # wave itself); a sponge band of 1.5 wavelengths must send back little.
+    depth, T, H = 0.5, 1.2, 0.01
+    om = 2 * math.pi / T
+    k = brentq(lambda k: G * depth * k * k * (1 + B15 * (k * depth) ** 2) / (1 + (B15 + 1 / 3) * (k * depth) ** 2) - om * om, 1e-6, 100)
+    Lw = 2 * math.pi / k
+    dx, dt, t_end = 0.05, 0.004, 24.0
+    n_short, n_long = 240, 800                     # 12 m and 40 m
+    probe = slice(int(1.0 / dx), int(6.0 / dx))    # 1 m to 6 m from the maker
+    ref = _channel_eta(n_long, 0, 0.0, dx, depth, T, H, t_end, dt)[probe]
+    wall = _channel_eta(n_short, 0, 0.0, dx, depth, T, H, t_end, dt)[probe]
+    sponge = _channel_eta(n_short, 1, 1.5 * Lw, dx, depth, T, H, t_end, dt)[probe]
+    nref = np.linalg.norm(ref)
+    assert nref > 0.3 * H / 2 * math.sqrt(probe.stop - probe.start)  # the incident wave is there
+    r_wall = np.linalg.norm(wall - ref) / nref
+    r_sponge = np.linalg.norm(sponge - ref) / nref
+    assert r_wall > 0.5, r_wall
+    assert r_sponge < 0.02 * r_wall, (r_sponge, r_wall)
+
+
+# ------------------------------------------------------------------ Euler start (Sec. 3.2.1, reading A12)
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_second_euler_step_adds_the_fstar_difference(mode):
+    # The second step is forward Euler too, and it carries the time-derivative
+    # terms as the difference of the dispersive fluxes of the last two levels:
+    # applying the operator of Eqs. 9-10 / 19-20 to P^2, Q^2 returns
+    # U*^1 + dt F^1 + (F*^1 - F*^0) and V*^1 + dt G^1 + (G*^1 - G*^0).  With the
+    # sequential cross form (cross_mode 1) the F* difference is the exact one
+    # across the step, F*(Q^2) - F*(Q^1).  Dropping the difference on this step,
+    # or using the first step's zero, fails the comparison.
+    case = W.barred_beach(nx=40, ny=36)
+    rng = np.random.default_rng(11)
+    P0 = 0.05 * rng.standard_normal((36, 40))
+    Q0 = 0.03 * rng.standard_normal((36, 40))
+    D = oracle.OracleDomain(dict(case["params"], bc=(0, 0, 0, 0), cross_mode=mode), case["bed"],
+                            None, None, P0, Q0)
+    r0 = D.rhs()
+    dt = 1e-3
+    D.step(dt)
+    U1, V1 = D.apply_T()
+    r1 = D.rhs()
+    D.step(dt)
+    U2, V2 = D.apply_T()
+    beta, gam = D.last_weights()
+    assert list(beta) == [dt, 0.0, 0.0]
+    dFs = (D.rhs()["Fs"] - r1["Fs"]) if mode == 1 else (r1["Fs"] - r0["Fs"])
+    dGs = r1["Gs"] - r0["Gs"]
+    assert np.abs(dGs).max() > 1e-3 * np.abs(r1["Gs"]).max() > 0  # the difference is not negligible
+    assert np.abs(dFs).max() > 1e-3 * np.abs(r1["Fs"]).max() > 0
+    np.testing.assert_allclose(U2, U1 + dt * r1["F"] + dFs, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(V2, V1 + dt * r1["G"] + dGs, rtol=1e-12, atol=1e-14)
