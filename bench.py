@@ -77,8 +77,57 @@ def peaks():
         return 6800.0, "fallback"
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes: the SM clock, its maximum and the
+    active clock event (throttle) reason bits of one GPU."""
+
+    # clock event reason bits of nvml.h
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+
+        self.ct = ctypes
+        self.L = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+            ok = self.L.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            idx = cuda_index
+            try:
+                idx = int(vis.split(",")[cuda_index]) if vis else cuda_index
+            except (ValueError, IndexError):
+                pass
+            if self.L.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) != 0:
+                raise RuntimeError("nvml handle")
+        v = ctypes.c_uint()
+        self.max_mhz = float(v.value) if self.L.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) == 0 else 0.0
+
+    def sample(self):
+        v = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(v)) != 0:
+            return None
+        fn = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.L.nvmlDeviceGetCurrentClocksThrottleReasons
+        bits = r.value if fn(self.h, self.ct.byref(r)) == 0 else 0
+        return float(v.value), bits
+
+
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and throttle reasons sampled during the timed region: an NVML
+    poller thread (about one sample per millisecond, so a region of a few
+    milliseconds is covered) and nvidia-smi every 200 ms beside it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -87,8 +136,27 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.nv = None
+        self.samples = []
+        self.lines = []
+
+    def _poll(self):
+        while not self._stop:
+            smp = self.nv.sample()
+            if smp is not None:
+                self.samples.append(smp)
+            time.sleep(0.001)
 
     def __enter__(self):
+        import threading
+
+        try:
+            self.nv = _Nvml(self.index)
+            self._stop = False
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+        except Exception:
+            self.nv = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -98,7 +166,9 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
-        self.lines = []
+        if self.nv is not None:
+            self._stop = True
+            self.th.join(timeout=2)
         if self.p is not None:
             self.p.terminate()
             try:
@@ -109,8 +179,6 @@ class Clocks:
             self.lines = [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
-        if not getattr(self, "lines", None):
-            return None
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
@@ -123,10 +191,18 @@ class Clocks:
             for k, nm in enumerate(names):
                 if len(f) > 5 + k and f[5 + k].lower().startswith("active"):
                     reasons.add(nm)
+        n_smi = len(sm)
+        if self.nv is not None and self.samples:
+            mx = max(mx, self.nv.max_mhz)
+            for mhz, bits in self.samples:
+                sm.append(mhz)
+                for b, nm in _Nvml.REASONS.items():
+                    if bits & b:
+                        reasons.add(nm)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "nvml_samples": len(sm) - n_smi, "smi_samples": n_smi}
 
 
 def dist_setup():
@@ -207,8 +283,9 @@ def run_reference(args):
             raise RuntimeError("oracle step failed %d" % rc)
     el = time.perf_counter() - t0
     value = p["nx"] * p["ny"] * args.steps / el
-    sample = "%s %dx%d (same layout, coarser grid), FP64, one oracle step per bench step" % (
-        args.workload, p["nx"], p["ny"])
+    full = (p["nx"], p["ny"]) == case_dims(args.workload, args.n)
+    sample = "%s %dx%d (%s), FP64, one oracle step per bench step, one thread" % (
+        args.workload, p["nx"], p["ny"], "the full grid" if full else "same layout, coarser grid")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
@@ -326,11 +403,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # bounded sample: the same layout on a 256 x 256 grid, ~15 s of oracle work
-        rate, nst, el = oracle_rate(make_case(args.workload, 256), 15.0)
-        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": "%s 256x256 (same layout, coarser grid), %d FP64 steps in %.1f s, one thread" % (
-                   args.workload, nst, el)}
+        cpu = run_cpu_baseline(args)
 
     if rank == 0:
         line = {
@@ -351,7 +424,7 @@ def run_ours(args):
             "kernel_ms": kms,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches * args.graph_steps * math.ceil(args.steps / args.graph_steps) + 2,
+            "gpu_launches": launches * args.steps + 2,
             "launches_per_step": launches,
             "fp64": fp64,
             "batched": batched,
@@ -364,6 +437,75 @@ def run_ours(args):
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+    return 0
+
+
+def cpu_model():
+    """CPU model name and logical core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.startswith("Model name:"):
+                model = l.split(":", 1)[1].strip()
+                break
+    except Exception:
+        model = None
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for l in f:
+                    if l.lower().startswith("model name"):
+                        model = l.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            model = None
+    import platform
+
+    return model or platform.machine(), os.cpu_count() or 1
+
+
+def run_cpu_baseline(args, seconds=6.0):
+    """The FP64 oracle, as it stands, on the host cores: bounded samples of the
+    solitary basin (256 x 64, its full 500 adaptive steps), the planar beach
+    (1024 x 256, the first steps of its run) and the benchmark workload at full
+    size (its first steps), each on one thread; then the planar-beach sample in
+    one independent oracle process per core at once (replicas: the oracle
+    itself stays single threaded)."""
+    rows = []
+    # (name, case, step cap, time cap): the solitary basin runs its 500 steps
+    for name, case, cap, tmax in (("solitary_basin_256x64", W.solitary_basin(), 500, 60.0),
+                                  ("planar_beach_1024x256", W.planar_beach(), 1000, seconds),
+                                  ("%s_%dx%d" % ((args.workload,) + case_dims(args.workload, args.n)),
+                                   make_case(args.workload, args.n), 200, seconds)):
+        rate, nst, el = oracle_rate(case, tmax, max_steps=cap)
+        rows.append({"workload": name, "steps": nst, "seconds": el, "value": rate, "cores": 1})
+    model, ncpu = cpu_model()
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", "planar_beach",
+                               "--worker-seconds", str(seconds)], stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(ncpu)]
+    total, ok = 0.0, 0
+    for pr in procs:
+        try:
+            out, _ = pr.communicate(timeout=600)
+            total += float(json.loads(out.strip().splitlines()[-1])["value"])
+            ok += 1
+        except Exception:
+            pr.kill()
+    head = rows[-1]
+    return {"value": head["value"], "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%s, %d FP64 steps in %.1f s, one thread (the full grid; the first steps of the run)" % (
+                head["workload"], head["steps"], head["seconds"]),
+            "cpu_model": model, "nproc": ncpu, "rows": rows,
+            "all_cores": {"value": total, "unit": "cell-updates/s", "cores": ok, "kind": "oracle replicas",
+                          "sample": "planar_beach_1024x256, one independent oracle process per core, "
+                                    "about %.0f s each" % seconds}}
+
+
+def oracle_worker(args):
+    """One oracle process of the all-cores row (no GPU use)."""
+    rate, nst, el = oracle_rate(make_case(args.oracle_worker, 1024), args.worker_seconds)
+    print(json.dumps({"value": rate, "steps": nst, "seconds": el}))
     return 0
 
 
@@ -424,7 +566,7 @@ def run_batched(args, dev, stream):
         "domains": len(cases), "cells": int(total), "precision": "fp32", "kahan": True,
         "value": value, "unit": "cell-updates/s", "ms_per_step": ms / args.batch_steps,
         "steps": args.batch_steps, "launches_per_step": launches, "autotuned_shapes": tuned,
-        "gpu_launches": launches * args.graph_steps * math.ceil(args.batch_steps / args.graph_steps) + 1,
+        "gpu_launches": launches * args.batch_steps + 1,
         "one_at_a_time_fp32": {"value": v32, "unit": "cell-updates/s", "steps_each": args.batch_solo_steps},
         "one_at_a_time_fp64": {"value": v64, "unit": "cell-updates/s", "steps_each": args.batch_fp64_steps},
         "speedup_vs_fp64_one_at_a_time": value / v64,
@@ -606,7 +748,11 @@ def main(argv=None):
     ap.add_argument("--batch-fp64-steps", type=int, default=16)
     ap.add_argument("--tune", type=lambda s: tuple(int(v) for v in s.split(",")), default=None,
                     help="kernel shape knobs (bsq_params.tune), comma separated")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--worker-seconds", type=float, default=6.0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
+    if args.oracle_worker:
+        return oracle_worker(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

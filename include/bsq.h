@@ -136,30 +136,44 @@ bsq_status bsq_create(const bsq_params *p, const double *bed_corners, const bsq_
                       const double *eta0, const double *P0, const double *Q0,
                       void *cuda_stream, bsq_domain **out);
 
-/* Advance with adaptive steps (Eqs. 22, 47) until t = t_end (the last step is
- * clamped to land on t_end) or max_steps more steps were taken (<= 0: no
- * limit).  *steps_done (may be NULL) receives the number taken.  Runs captured
- * CUDA graphs of graph_steps steps; steps past the end inside a graph do no
- * work.  Errors: BSQ_ERR_NONFINITE, BSQ_ERR_UNSTABLE, BSQ_ERR_TIMEOUT,
- * BSQ_ERR_CUDA. */
+/* Advance with adaptive steps (Eqs. 22, 47; AB3 of Eqs. 42-46 after the Euler
+ * start of Sec. 3.2.1) until t = t_end (the last step is clamped to land on
+ * t_end) or max_steps more steps were taken (<= 0: no limit; then t_end must
+ * be finite).  *steps_done (may be NULL) receives the number taken.  Runs
+ * captured CUDA graphs of graph_steps steps and single steps for the
+ * remainder: with max_steps it enqueues exactly max_steps step slots, toward
+ * t_end about the steps the last step size says are left, and slots past the
+ * end do no work.  Errors: BSQ_ERR_ARG, BSQ_ERR_NONFINITE, BSQ_ERR_UNSTABLE,
+ * BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
 bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done);
 
-/* Take n steps with the given step sizes dts[0..n-1] (host array), instead of
- * the CFL rule: replays a recorded dt sequence. */
+/* Take n steps with the given step sizes dts[0..n-1] (host array, each > 0 and
+ * finite) instead of the CFL rule of Eq. 22 and the moving average of Eq. 47:
+ * replays a recorded dt sequence through the same update (Euler start of
+ * Sec. 3.2.1, then the variable-step weights of Eqs. 42-46 for those steps).
+ * The steps are launched one by one (no graph).  Errors: BSQ_ERR_ARG (NULL
+ * dts with n > 0, n < 0, a step not > 0), BSQ_ERR_NONFINITE, BSQ_ERR_TIMEOUT,
+ * BSQ_ERR_CUDA. */
 bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n);
 
 /* Copy one field of the interior (BSQ_FIELD_*) to host_out (nx*ny doubles,
- * caller-owned).  FP32 values are widened to double.  Waits for the domain's
- * stream (bounded). */
+ * caller-owned, row-major with x fastest).  The state variables are those of
+ * Eq. 5 (w, P = hu, Q = hv); ETA is h - d of Sec. 2 with h = max(w - b, 0)
+ * and d = max(w_s - b, 0), H is h, W is w.  FP32 values are widened to
+ * double.  Waits for the domain's stream (bounded).  Errors: BSQ_ERR_ARG
+ * (NULL, unknown field), BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA, the sticky error. */
 bsq_status bsq_read(const bsq_domain *d, int field, double *host_out);
 
 /* Copy one field of the interior to device memory dev_out (nx*ny elements of
  * the domain's precision, caller-owned), enqueued on the domain's stream. */
 bsq_status bsq_read_device(const bsq_domain *d, int field, void *dev_out);
 
-/* Simulated time, steps taken, last step size, mass sum(h) dx dy and the
- * number of positivity clamps (w raised to b after an update) so far.
- * Any pointer may be NULL.  Waits for the domain's stream (bounded). */
+/* Simulated time t_n, steps taken n, the last step size dt_{n-1} (Eq. 22
+ * with Eq. 47), the water volume sum(h) dx dy (conserved by the finite-volume
+ * update of Sec. 3 in a closed basin) and the number of positivity clamps (w
+ * raised to b after an update, keeping h >= 0 as Sec. 3.5 requires) so far.
+ * Any pointer may be NULL.  Waits for the domain's stream (bounded).  Errors:
+ * BSQ_ERR_ARG (NULL domain), BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
 bsq_status bsq_info(const bsq_domain *d, double *t, long long *n, double *last_dt, double *mass,
                     long long *clamps);
 

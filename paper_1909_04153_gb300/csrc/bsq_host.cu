@@ -9,6 +9,7 @@
 // runs captured CUDA graphs of whole steps; the only host-device traffic per
 // graph is the launch and a 64-byte status read.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -548,6 +549,29 @@ static bsq_status build_graph(bsq_domain *d)
     return BSQ_OK;
 }
 
+// Steps a run to t_end probably still needs, from the last step size (the
+// adaptive step changes slowly: Eq. 47 lets it rise gradually); -1 when there
+// is no estimate (no finite end, or no step taken yet).
+static long long steps_left_estimate(double t, double t_end, double last_dt)
+{
+    if (!isfinite(t_end) || !(last_dt > 0.0)) return -1;
+    const double r = (t_end - t) / last_dt;
+    if (!(r > 0.0)) return 1;
+    return (long long)fmin(1.05 * r + 1.0, 1e15);
+}
+
+// How many step slots to enqueue before the next look at the controller
+// state: the steps still allowed (budget), cut to the estimate of the steps
+// left to t_end, without an estimate graph_steps x grow; at most 64 graphs.
+static long long steps_to_enqueue(long long budget, long long est, int gs, int grow)
+{
+    long long want = budget;
+    if (est > 0) want = est < want ? est : want;
+    else if (budget == LLONG_MAX) want = (long long)gs * grow;
+    const long long cap = 64LL * gs;
+    return want < cap ? want : cap;
+}
+
 extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done)
 {
     cudaGetLastError();  // a failed call of another domain must not be reported here
@@ -561,34 +585,26 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
     st = build_graph(d);
     if (st != BSQ_OK) return set_sticky(d, st);
     if (cudaSuccess != enqueue_start(d, t_end, max_steps, 0.0)) return set_sticky(d, BSQ_ERR_CUDA);
-    if (st != BSQ_OK) return set_sticky(d, st);
-    if (max_steps > 0) {
-        long long ng = (max_steps + d->graph_steps - 1) / d->graph_steps;
-        const long long chunk = 64;
-        for (long long q = 0; q < ng; q += chunk) {
-            long long m = ng - q < chunk ? ng - q : chunk;
-            for (long long r = 0; r < m; r++)
-                if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
-            st = read_ctl(d);
-            if (st != BSQ_OK) return set_sticky(d, st);
-            st = ctl_status(*d->h_ctl);
-            if (st != BSQ_OK) break;
-            double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
-            if (!(d->h_ctl->t < t_end - tol)) break;
-        }
-    } else {
-        int batch = 1;
-        for (;;) {
-            for (int r = 0; r < batch; r++)
-                if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
-            st = read_ctl(d);
-            if (st != BSQ_OK) return set_sticky(d, st);
-            st = ctl_status(*d->h_ctl);
-            if (st != BSQ_OK) break;
-            double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
-            if (!(d->h_ctl->t < t_end - tol)) break;
-            if (batch < 64) batch *= 2;
-        }
+    // Whole graphs of graph_steps steps, then the remainder as single steps,
+    // so a call runs exactly the step slots it may need: max_steps of them,
+    // or about the steps left to t_end (slots past the end do no work).
+    const double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
+    long long budget = max_steps > 0 ? max_steps : LLONG_MAX;
+    int grow = 1;
+    for (;;) {
+        const long long est = steps_left_estimate(d->h_ctl->t, t_end, d->h_ctl->last_dt);
+        const long long m = steps_to_enqueue(budget, est, d->graph_steps, grow);
+        for (long long r = 0; r < m / d->graph_steps; r++)
+            if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+        for (long long r = 0; r < m % d->graph_steps; r++)
+            if (enqueue_step(d, 0.0) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+        if (budget != LLONG_MAX) budget -= m;
+        st = read_ctl(d);
+        if (st != BSQ_OK) return set_sticky(d, st);
+        st = ctl_status(*d->h_ctl);
+        if (st != BSQ_OK) break;
+        if (!(d->h_ctl->t < t_end - tol) || budget <= 0) break;
+        if (grow < 64) grow *= 2;
     }
     if (steps_done) *steps_done = d->h_ctl->n - n0;
     return set_sticky(d, st);
@@ -974,19 +990,32 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
         }
         return true;
     };
-    long long launched = 0;
-    const long long cap = max_steps > 0 ? (max_steps + b->graph_steps - 1) / b->graph_steps : -1;
-    int chunk = 1;
+    // whole graphs, then the remainder as single batched steps (as bsq_advance)
+    long long budget = max_steps > 0 ? max_steps : LLONG_MAX;
+    int grow = 1;
     for (;;) {
-        long long m = chunk;
-        if (cap >= 0 && launched + m > cap) m = cap - launched;
-        for (long long r = 0; r < m; r++)
+        long long est = -1;  // most steps any unfinished member probably still needs
+        bool unknown = false;
+        for (int d = 0; d < n; d++) {
+            const Ctl &c = b->h_ctl[d];
+            if (ctl_status(c) != BSQ_OK || (max_steps > 0 && c.n - n0[d] >= max_steps)) continue;
+            const long long e = steps_left_estimate(c.t, b->h_tend[d], c.last_dt);
+            if (e < 0) unknown = true;
+            else if (e > est) est = e;
+        }
+        const long long m = steps_to_enqueue(budget, unknown ? -1 : est, b->graph_steps, grow);
+        for (long long r = 0; r < m / b->graph_steps; r++)
             if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return BSQ_ERR_CUDA;
-        launched += m;
+        for (long long r = 0; r < m % b->graph_steps; r++) {
+            cudaError_t e2 = b->fp64 ? launch_batch_step<double>((const Dev<double> *)b->Ds, b->plan, b->stream)
+                                     : launch_batch_step<float>((const Dev<float> *)b->Ds, b->plan, b->stream);
+            if (e2 != cudaSuccess) return BSQ_ERR_CUDA;
+        }
+        if (budget != LLONG_MAX) budget -= m;
         st = batch_read_ctl(b);
         if (st != BSQ_OK) return st;
-        if (all_done() || (cap >= 0 && launched >= cap)) break;
-        if (chunk < 64) chunk *= 2;
+        if (all_done() || budget <= 0) break;
+        if (grow < 64) grow *= 2;
     }
     bsq_status first = BSQ_OK;
     for (int d = 0; d < n; d++) {

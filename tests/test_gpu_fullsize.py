@@ -5,7 +5,14 @@ oracle's dt sequence replayed:
 * solitary wave, 256 x 64, 500 steps (the whole run);
 * JONSWAP waves on a 1:20 beach, 1024 x 256, 1000 steps;
 * barred beach with rip channels, 2048 x 2048, 3 steps (the oracle needs
-  seconds per step at this size), compared on every cell.
+  seconds per step at this size), compared on every cell;
+* the same barred beach on a 512 x 512 grid (same layout, 0.1 m cells), 1000
+  steps, the single-precision path against the oracle once the waves have
+  grown (no absolute fallback);
+* the barred beach at 2048 x 2048 for 20,000 steps: single precision with
+  compensated accumulation against the double-precision path (which the
+  tests above hold to the oracle), the FP64 run's adaptive step sequence
+  replayed, relative L2 and largest cell error per field.
 """
 import numpy as np
 import pytest
@@ -78,3 +85,44 @@ def test_hamm_rip_full_size_adaptive_run():
         h = d.read("h")
         assert np.isfinite(h).all() and (h >= 0).all()
         assert info["n"] == 601 and 0.0 < info["last_dt"] < 0.003
+
+
+def linf(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_barred_beach_512_fp32_1000_steps_matches_oracle():
+    case = W.barred_beach(nx=512, ny=512)
+    o, dts = _run_oracle(case, 1000)
+    ref = o.get("eta")
+    assert np.sqrt(np.mean(ref ** 2)) > 1e-3  # the waves have grown
+    with bsq.Domain(case, precision="fp32", kahan=True) as d:
+        d.step_dt(dts)
+        e = rel(d.read("eta"), ref)
+        assert e <= 1e-4, e
+        for f in ("P", "Q"):
+            assert rel(d.read(f), o.get(f)) <= 1e-3, f
+        assert d.info()["clamps"] == o.info()["clamps"]
+
+
+def test_barred_beach_2048_fp32_against_fp64_20000_steps():
+    case = W.barred_beach()
+    steps = 20000
+    with bsq.Domain(case, precision="fp64") as d64:
+        dts = []
+        for _ in range(steps):
+            assert d64.advance(max_steps=1) == 1
+            dts.append(d64.info()["last_dt"])
+        ref = {f: d64.read(f) for f in ("eta", "P", "Q")}
+        t64 = d64.info()["t"]
+    with bsq.Domain(case, precision="fp32", kahan=True) as d32:
+        d32.step_dt(dts)
+        assert abs(d32.info()["t"] - t64) <= 1e-12 * t64
+        got = {f: d32.read(f) for f in ("eta", "P", "Q")}
+    report = {f: (rel(got[f], ref[f]), linf(got[f], ref[f])) for f in ref}
+    print("barred_beach 2048x2048, %d steps to t = %.4f s, FP32+Kahan against FP64 "
+          "(relative L2, largest cell error / field max): %s" % (
+              steps, t64, ", ".join("%s %.3e %.3e" % (f, a, b) for f, (a, b) in report.items())))
+    for f in ("eta", "P", "Q"):
+        assert np.isfinite(got[f]).all()
+    assert report["eta"][0] <= 1e-3, report
