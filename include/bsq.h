@@ -86,22 +86,18 @@ typedef struct {
     int kahan;             /* FP32: compensated accumulation of w, P, Q increments */
     int cross_mode;        /* BSQ_CROSS_* */
     int graph_steps;       /* steps per captured CUDA graph in bsq_advance; <= 0: 16 */
-    int tune[8];           /* kernel shape knobs, 0 = default: [0] block-scan y-solver rows per
-                              thread (8, 16, 32), [1] its threads per block (32..512) -- either
-                              selects the block-scan y-solver over the three-launch one;
-                              [2] bit 0: RHS kernel (0 sliding window, 1 shared-memory tiles),
-                              bit 1: x-solver without shared-memory staging, bit 2: x-solver
-                              with two rows in flight per block, bit 3: persistent x-solver
-                              with one row in flight, bit 4: x-solver with one warp per row
-                              (the single-precision default); [3] rows per warp
-                              of the sliding window (16, 24, 32, 48, 64; 16 selects the
+    int tune[8];           /* kernel shape knobs, 0 = default: [0], [1] reserved;
+                              [2] x-solver: bit 1 registers only (no staging), bit 3 the
+                              persistent solver with two staged rows (the double-precision
+                              default where its rows fit), bit 4 one warp per row (the
+                              single-precision default); [3] rows per warp of the
+                              sliding-window RHS (16, 24, 32, 48, 64; 16 selects the
                               one-column kernel, which takes 24 and 48 as 32; 0: by grid
-                              size); [4] x-solver elements per
-                              thread (4, 8, 16, 32); [5] rows per chunk of the three-launch
-                              y-solver (8, 16); [6] bit 0: its chunk summaries by a kernel
-                              of their own instead of inside the RHS kernel, bit 1: one column
-                              per lane in the single-precision RHS kernel (instead of two,
-                              paired); [7] reserved */
+                              size); [4] x-solver elements per thread (4, 8, 16, 32);
+                              [5] rows per y-line chunk (8, 16); [6] bit 0: the chunk
+                              summaries by a kernel of their own instead of inside the RHS
+                              kernel, bit 1: one column per lane in the single-precision RHS
+                              kernel (instead of two, paired); [7] reserved */
 } bsq_params;
 
 /* Most wave-maker components a domain takes. */

@@ -301,15 +301,12 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.eps = (T)eps;
     D.kahan = kahan ? 1 : 0;
     D.cross_mode = p.cross_mode;
-    D.tune_ykch = p.tune[0] == 8 || p.tune[0] == 16 || p.tune[0] == 32 ? p.tune[0] : 0;
-    D.tune_ythreads = p.tune[1] >= 32 && p.tune[1] <= 512 ? p.tune[1] : 0;
-    D.tune_rhs = (p.tune[2] & 1) ? 1 : 0;
     D.tune_rows = p.tune[3] == 16 || p.tune[3] == 24 || p.tune[3] == 32 || p.tune[3] == 48 || p.tune[3] == 64
                       ? p.tune[3]
                       : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;
     D.tune_rhs1 = (p.tune[6] & 2) ? 1 : 0;
-    D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 4) ? 2 : ((p.tune[2] & 2) ? 1 : 0)));
+    D.tune_xtma = (p.tune[2] & 16) ? 4 : ((p.tune[2] & 8) ? 3 : ((p.tune[2] & 2) ? 1 : 0));
     D.tune_xk = (p.tune[4] == 4 || p.tune[4] == 8 || p.tune[4] == 16 || p.tune[4] == 32) ? p.tune[4] : 0;
     D.tune_yk = (p.tune[5] == 8 || p.tune[5] == 16) ? p.tune[5] : 0;
     {
@@ -355,7 +352,6 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     dm->coef = D.coef;
     dm->mass_partial = (double *)(base + o_mass);
     // explicit y-solver shapes, or columns of more than 256 chunks, select the block-scan kernel
-    D.ysplit = (p.tune[0] == 0 && p.tune[1] == 0 && ysplit_chunks<T>(ny, D.tune_yk) <= 256) ? 1 : 0;
     D.ysums = (T *)(base + o_ysum);
     D.yin = D.ysums + 5 * nchy;
     D.yxa = D.ysums + 6 * nchy;
@@ -697,7 +693,7 @@ static bsq_status batch_build(bsq_batch *b, int rows, int K, int KY)
     std::vector<Dev<T>> hD(n);
     for (int d = 0; d < n; d++) {
         const Dev<T> &D = dev_of<T>(b->doms[d]);
-        if (!D.ysplit || D.tune_yk != 0 || D.tune_xk != 0) return BSQ_ERR_ARG;
+        if (D.tune_yk != 0 || D.tune_xk != 0) return BSQ_ERR_ARG;
         fast = fast && D.theta == (T)1 && D.cross_mode != 0 && D.friction == (T)0 &&
                (D.kahan != 0) == (sizeof(T) == 4) && D.fstride * 15 < 0x7fffffffLL;
         theta1 = theta1 && D.theta == (T)1;

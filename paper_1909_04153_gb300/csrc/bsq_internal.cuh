@@ -53,12 +53,10 @@ struct Dev {
     double dxd, dyd;          // cell sizes in FP64 (wave-maker phases)
     T g, Bd, eps, w_s, friction, theta;
     int kahan, cross_mode;
-    int tune_ykch, tune_ythreads;  // y-solver chunk rows and block size (0: default)
-    int tune_rhs, tune_rows;       // RHS kernel variant (0 sliding window, 1 tiled), rows per warp
-    int tune_xtma;                 // 0: TMA-staged x-solver when it fits, 1: register version
+    int tune_rows;                 // RHS rows per warp (0: by grid size)
+    int tune_xtma;                 // x-solver: 0 automatic, 1 registers only, 3 persistent, 4 warp per row
     int nsm;                       // multiprocessors of the device
     int tune_xk, tune_yk;          // x-solver elements per thread, split y-solver rows per chunk (0: default)
-    int ysplit;                    // 1: three-launch y-solver (summaries, scans, apply)
     int tune_ysum;                 // 1: chunk summaries by their own kernel, not in the RHS kernel
     int tune_rhs1;                 // 1: one column per lane in the sliding-window RHS (single precision)
     T *ysums, *yin, *yxa;          // its chunk summaries (5 per chunk) and scanned values

@@ -682,249 +682,6 @@ __device__ __forceinline__ void reconstruct(T wm, T w0, T wp, T Pm, T P0, T Pp, 
     Ql = Q0 - (T)0.5 * sQ; Qh = Q0 + (T)0.5 * sQ;
 }
 
-// Central-upwind flux across one face; DIR 0: x-face, 1: y-face.
-template <typename T, int DIR>
-__device__ __forceinline__ void cu_flux(T bf, T wL, T PL, T QL, T wR, T PR, T QR, T g, T eps,
-                                        T &H0, T &H1, T &H2)
-{
-    T hL = tmax(wL - bf, (T)0), hR = tmax(wR - bf, (T)0);
-    T iL = (T)BSQ_SQRT2 * hL * desing_inv(hL, eps);
-    T iR = (T)BSQ_SQRT2 * hR * desing_inv(hR, eps);
-    T uL = iL * PL, vL = iL * QL, uR = iR * PR, vR = iR * QR;
-    T pL = hL * uL, qL = hL * vL, pR = hR * uR, qR = hR * vR;
-    T cL = tsqrt(g * hL), cR = tsqrt(g * hR);
-    T unL = DIR == 0 ? uL : vL, unR = DIR == 0 ? uR : vR;
-    T ap = tmax(tmax(unL + cL, unR + cR), (T)0);
-    T am = tmin(tmin(unL - cL, unR - cR), (T)0);
-    T den = ap - am;
-    if (!(den > (T)0)) { H0 = H1 = H2 = (T)0; return; }
-    T inv = (T)1 / den;
-    T FL0, FL1, FL2, FR0, FR1, FR2;
-    if (DIR == 0) {
-        FL0 = pL; FL1 = pL * uL + (T)0.5 * g * hL * hL; FL2 = qL * uL;
-        FR0 = pR; FR1 = pR * uR + (T)0.5 * g * hR * hR; FR2 = qR * uR;
-    } else {
-        FL0 = qL; FL1 = pL * vL; FL2 = qL * vL + (T)0.5 * g * hL * hL;
-        FR0 = qR; FR1 = pR * vR; FR2 = qR * vR + (T)0.5 * g * hR * hR;
-    }
-    T k = ap * am * inv;
-    H0 = (ap * FL0 - am * FR0) * inv + k * (hR - hL);
-    H1 = (ap * FL1 - am * FR1) * inv + k * (pR - pL);
-    H2 = (ap * FL2 - am * FR2) * inv + k * (qR - qL);
-}
-
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_rhs_combine(Dev<T> D)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    constexpr int SX = TX + 4, SY = TY + 4;
-    __shared__ T sw[SY][SX], sP[SY][SX], sQ[SY][SX], sEta[SY][SX], sD[SY][SX], sB[SY][SX];
-    __shared__ T sK[SY + 1][SX + 1];
-    __shared__ T sHx[3][TY][TX + 1];
-    __shared__ T sHy[3][TY + 1][TX];
-
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int nx = D.nx, ny = D.ny;
-    const T *w = D.w[cf.wc];
-
-    // 1. stage w, P, Q (2-cell halo) and the bed corners
-    for (int q = tid; q < SX * SY; q += TX * TY) {
-        int a = q % SX, b = q / SX;
-        int i = min(i0 + a - 2, nx + 1), j = min(j0 + b - 2, ny + 1);
-        long long c = fidx(D, i, j);
-        sw[b][a] = w[c];
-        sP[b][a] = D.P[c];
-        sQ[b][a] = D.Q[c];
-    }
-    for (int q = tid; q < (SX + 1) * (SY + 1); q += TX * TY) {
-        int a = q % (SX + 1), b = q / (SX + 1);
-        int i = min(i0 + a - 2, nx + 2), j = min(j0 + b - 2, ny + 2);
-        sK[b][a] = D.corner[(long long)(j + 2) * D.cpitch + (i + 2)];
-    }
-    __syncthreads();
-    // 2. cell-centre bed (mean of the 4 face values), still depth, eta = h - d
-    for (int q = tid; q < SX * SY; q += TX * TY) {
-        int a = q % SX, b = q / SX;
-        T bw = (T)0.5 * (sK[b][a] + sK[b + 1][a]);
-        T be = (T)0.5 * (sK[b][a + 1] + sK[b + 1][a + 1]);
-        T bs = (T)0.5 * (sK[b][a] + sK[b][a + 1]);
-        T bn = (T)0.5 * (sK[b + 1][a] + sK[b + 1][a + 1]);
-        T bc = (T)0.25 * (bw + be + bs + bn);
-        T d = tmax(D.w_s - bc, (T)0);
-        sB[b][a] = bc;
-        sD[b][a] = d;
-        sEta[b][a] = tmax(sw[b][a] - bc, (T)0) - d;
-    }
-    __syncthreads();
-    // 3. face fluxes: x-faces (TX+1) x TY, then y-faces TX x (TY+1)
-    const T th = D.theta, g = D.g, eps = D.eps;
-    for (int q = tid; q < (TX + 1) * TY + TX * (TY + 1); q += TX * TY) {
-        if (q < (TX + 1) * TY) {
-            int fa = q % (TX + 1), r = q / (TX + 1);
-            int b = r + 2, aL = fa + 1, aR = fa + 2;
-            T bf = (T)0.5 * (sK[b][aR] + sK[b + 1][aR]);
-            T bLw = (T)0.5 * (sK[b][aL] + sK[b + 1][aL]);
-            T bRe = (T)0.5 * (sK[b][aR + 1] + sK[b + 1][aR + 1]);
-            T wl, wh, Pl, Ph, Ql, Qh, wl2, wh2, Pl2, Ph2, Ql2, Qh2;
-            reconstruct(sw[b][aL - 1], sw[b][aL], sw[b][aL + 1], sP[b][aL - 1], sP[b][aL], sP[b][aL + 1],
-                        sQ[b][aL - 1], sQ[b][aL], sQ[b][aL + 1], bLw, bf, th, wl, wh, Pl, Ph, Ql, Qh);
-            reconstruct(sw[b][aR - 1], sw[b][aR], sw[b][aR + 1], sP[b][aR - 1], sP[b][aR], sP[b][aR + 1],
-                        sQ[b][aR - 1], sQ[b][aR], sQ[b][aR + 1], bf, bRe, th, wl2, wh2, Pl2, Ph2, Ql2, Qh2);
-            T H0, H1, H2;
-            cu_flux<T, 0>(bf, wh, Ph, Qh, wl2, Pl2, Ql2, g, eps, H0, H1, H2);
-            sHx[0][r][fa] = H0; sHx[1][r][fa] = H1; sHx[2][r][fa] = H2;
-        } else {
-            int q2 = q - (TX + 1) * TY;
-            int c = q2 % TX, fb = q2 / TX;
-            int a = c + 2, bL = fb + 1, bU = fb + 2;
-            T bf = (T)0.5 * (sK[bU][a] + sK[bU][a + 1]);
-            T bLs = (T)0.5 * (sK[bL][a] + sK[bL][a + 1]);
-            T bUn = (T)0.5 * (sK[bU + 1][a] + sK[bU + 1][a + 1]);
-            T wl, wh, Pl, Ph, Ql, Qh, wl2, wh2, Pl2, Ph2, Ql2, Qh2;
-            reconstruct(sw[bL - 1][a], sw[bL][a], sw[bL + 1][a], sP[bL - 1][a], sP[bL][a], sP[bL + 1][a],
-                        sQ[bL - 1][a], sQ[bL][a], sQ[bL + 1][a], bLs, bf, th, wl, wh, Pl, Ph, Ql, Qh);
-            reconstruct(sw[bU - 1][a], sw[bU][a], sw[bU + 1][a], sP[bU - 1][a], sP[bU][a], sP[bU + 1][a],
-                        sQ[bU - 1][a], sQ[bU][a], sQ[bU + 1][a], bf, bUn, th, wl2, wh2, Pl2, Ph2, Ql2, Qh2);
-            T H0, H1, H2;
-            cu_flux<T, 1>(bf, wh, Ph, Qh, wl2, Pl2, Ql2, g, eps, H0, H1, H2);
-            sHy[0][fb][c] = H0; sHy[1][fb][c] = H1; sHy[2][fb][c] = H2;
-        }
-    }
-    __syncthreads();
-
-    // 4. per interior cell: E, F, G, F*, G* and the AB3 combine
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = i0 + tx, j = j0 + ty;
-    bool clamped = false;
-    if (i < nx && j < ny) {
-        const int a = tx + 2, b = ty + 2;
-        const T rdx = D.rdx, rdy = D.rdy;
-        T divx0 = (sHx[0][ty][tx + 1] - sHx[0][ty][tx]) * rdx;
-        T divx1 = (sHx[1][ty][tx + 1] - sHx[1][ty][tx]) * rdx;
-        T divx2 = (sHx[2][ty][tx + 1] - sHx[2][ty][tx]) * rdx;
-        T divy0 = (sHy[0][ty + 1][tx] - sHy[0][ty][tx]) * rdy;
-        T divy1 = (sHy[1][ty + 1][tx] - sHy[1][ty][tx]) * rdy;
-        T divy2 = (sHy[2][ty + 1][tx] - sHy[2][ty][tx]) * rdy;
-        T bW = (T)0.5 * (sK[b][a] + sK[b + 1][a]);
-        T bE = (T)0.5 * (sK[b][a + 1] + sK[b + 1][a + 1]);
-        T bS = (T)0.5 * (sK[b][a] + sK[b][a + 1]);
-        T bN = (T)0.5 * (sK[b + 1][a] + sK[b + 1][a + 1]);
-        T w0 = sw[b][a], P0 = sP[b][a], Q0 = sQ[b][a], bc = sB[b][a];
-        T srcx = -g * (bE - bW) * rdx * (w0 - (T)0.5 * (bE + bW));
-        T srcy = -g * (bN - bS) * rdy * (w0 - (T)0.5 * (bN + bS));
-        T fr1 = (T)0, fr2 = (T)0;
-        if (D.friction != (T)0) {
-            T h = tmax(w0 - bc, (T)0);
-            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, eps);
-            T u = iv * P0, v = iv * Q0;
-            T sp = tsqrt(u * u + v * v);
-            fr1 = D.friction * u * sp;
-            fr2 = D.friction * v * sp;
-        }
-        // dispersive central differences (Eqs. 12-15)
-        const T d = sD[b][a];
-        const T half_rdx = (T)0.5 * rdx, half_rdy = (T)0.5 * rdy;
-        const T ddx = (sD[b][a + 1] - sD[b][a - 1]) * half_rdx;
-        const T ddy = (sD[b + 1][a] - sD[b - 1][a]) * half_rdy;
-        const T rdx2 = rdx * rdx, rdy2 = rdy * rdy;
-        T e_xx = (sEta[b][a + 1] - (T)2 * sEta[b][a] + sEta[b][a - 1]) * rdx2;
-        T e_yy = (sEta[b + 1][a] - (T)2 * sEta[b][a] + sEta[b - 1][a]) * rdy2;
-        T e_xy = (sEta[b + 1][a + 1] - sEta[b - 1][a + 1] - sEta[b + 1][a - 1] + sEta[b - 1][a - 1]) *
-                 ((T)0.25 * rdx * rdy);
-        T e_xxx = (sEta[b][a + 2] - (T)2 * sEta[b][a + 1] + (T)2 * sEta[b][a - 1] - sEta[b][a - 2]) *
-                  ((T)0.5 * rdx2 * rdx);
-        T e_yyy = (sEta[b + 2][a] - (T)2 * sEta[b + 1][a] + (T)2 * sEta[b - 1][a] - sEta[b - 2][a]) *
-                  ((T)0.5 * rdy2 * rdy);
-        T eyy_p = (sEta[b + 1][a + 1] - (T)2 * sEta[b][a + 1] + sEta[b - 1][a + 1]) * rdy2;
-        T eyy_m = (sEta[b + 1][a - 1] - (T)2 * sEta[b][a - 1] + sEta[b - 1][a - 1]) * rdy2;
-        T exx_p = (sEta[b + 1][a + 1] - (T)2 * sEta[b + 1][a] + sEta[b + 1][a - 1]) * rdx2;
-        T exx_m = (sEta[b - 1][a + 1] - (T)2 * sEta[b - 1][a] + sEta[b - 1][a - 1]) * rdx2;
-        T e_xyy = (eyy_p - eyy_m) * half_rdx;
-        T e_xxy = (exx_p - exx_m) * half_rdy;
-        const T Bg = D.Bd * g;
-        T dispx = Bg * d * d * d * (e_xxx + e_xyy) + Bg * d * d * (ddx * ((T)2 * e_xx + e_yy) + ddy * e_xy);
-        T dispy = Bg * d * d * d * (e_yyy + e_xxy) + Bg * d * d * (ddy * ((T)2 * e_yy + e_xx) + ddx * e_xy);
-        T E = -divx0 - divy0;
-        T F = -divx1 - divy1 + srcx - fr1 + dispx;
-        T G = -divx2 - divy2 + srcy - fr2 + dispy;
-        const T kB = D.Bd + (T)1 / (T)3;
-        const T sixth = (T)1 / (T)6;
-        T Q_x = (sQ[b][a + 1] - sQ[b][a - 1]) * half_rdx;
-        T Q_y = (sQ[b + 1][a] - sQ[b - 1][a]) * half_rdy;
-        T Q_xy = (sQ[b + 1][a + 1] - sQ[b - 1][a + 1] - sQ[b + 1][a - 1] + sQ[b - 1][a - 1]) *
-                 ((T)0.25 * rdx * rdy);
-        T P_x = (sP[b][a + 1] - sP[b][a - 1]) * half_rdx;
-        T P_y = (sP[b + 1][a] - sP[b - 1][a]) * half_rdy;
-        T P_xy = (sP[b + 1][a + 1] - sP[b - 1][a + 1] - sP[b + 1][a - 1] + sP[b - 1][a - 1]) *
-                 ((T)0.25 * rdx * rdy);
-        T Fs = d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
-        T Gs = d * ddy * P_x * sixth + d * ddx * P_y * sixth + kB * d * d * P_xy;
-
-        // AB3 / Euler combine (Eqs. 42-43)
-        const long long c = fidx(D, i, j);
-        const long long fs = D.fstride;
-        T *H = D.hist;
-        const T b0 = coefv<T>(cf, 0, 0), b1 = coefv<T>(cf, 0, 1), b2 = coefv<T>(cf, 0, 2);
-        const T g0 = coefv<T>(cf, 1, 0), g1 = coefv<T>(cf, 1, 1), g2 = coefv<T>(cf, 1, 2);
-        T dw = b0 * E, dU = b0 * F, dV = b0 * G + g0 * Gs;
-        const bool extrap = D.cross_mode == 0;
-        if (extrap) dU += g0 * Fs;
-        if (cf.nlev >= 2) {
-            const long long o = (long long)cf.s1 * fs + c;
-            dw += b1 * H[0 * 3 * fs + o];
-            dU += b1 * H[1 * 3 * fs + o];
-            dV += b1 * H[2 * 3 * fs + o] + g1 * H[4 * 3 * fs + o];
-            if (extrap) dU += g1 * H[3 * 3 * fs + o];
-        }
-        if (cf.nlev >= 3) {
-            const long long o = (long long)cf.s2 * fs + c;
-            dw += b2 * H[0 * 3 * fs + o];
-            dU += b2 * H[1 * 3 * fs + o];
-            dV += b2 * H[2 * 3 * fs + o] + g2 * H[4 * 3 * fs + o];
-            if (extrap) dU += g2 * H[3 * 3 * fs + o];
-        }
-        if (!extrap) dU -= Fs;  // F*(Q^{n+1}) is added by the x-line kernel
-        {
-            const long long o = (long long)cf.s0 * fs + c;
-            H[0 * 3 * fs + o] = E;
-            H[1 * 3 * fs + o] = F;
-            H[2 * 3 * fs + o] = G;
-            if (extrap) H[3 * 3 * fs + o] = Fs;
-            H[4 * 3 * fs + o] = Gs;
-        }
-        // w^{n+1} = w^n + dw with compensated accumulation, then h >= 0
-        T wn, cwn = (T)0;
-        if (D.kahan) {
-            T cw = D.cw[c];
-            T y = dw - cw;
-            wn = w0 + y;
-            cwn = (wn - w0) - y;
-        } else {
-            wn = w0 + dw;
-        }
-        if (wn < bc) { wn = bc; cwn = (T)0; clamped = true; }
-        D.w[cf.wc ^ 1][c] = wn;
-        if (D.kahan) D.cw[c] = cwn;
-        D.dU[c] = dU;
-        D.dV[c] = dV;
-    }
-    int nclamp = __syncthreads_count(clamped);
-    if (tid == 0 && nclamp) atomicAdd(&D.ctl->clamps, (unsigned long long)nclamp);
-    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
-        // commit the step in the controller state (the controller kernel of
-        // this step has finished; no block of this kernel reads Ctl)
-        Ctl *ct = D.ctl;
-        ct->dtm2 = ct->dtm1;
-        ct->dtm1 = cf.dt;
-        ct->last_dt = cf.dt;
-        ct->t = cf.t1;
-        ct->n = cf.n + 1;
-        ct->rate_bits = 0ull;
-    }
-}
-
 // ------------------------------------------------------------------ RHS + combine, sliding window
 
 // Face state of KP07 on one side of a face: depth and desingularised velocities
@@ -1682,107 +1439,6 @@ __global__ void __launch_bounds__(128, 2) k_rhs_sw2(Dev<float> D, int nstrip, in
 
 // ------------------------------------------------------------------ y-line solves
 
-// Thread (column c, chunk k) owns rows [k*KCH, (k+1)*KCH) of one column.
-// Forward elimination y_j = m_j r_j + e_j y_{j-1} and back substitution
-// x_j = y_j - c'_j x_{j+1} are affine recurrences: each thread composes its
-// chunk, a block scan over the chunks of a column supplies the value entering
-// each chunk, and the chunk is finished from registers.
-template <typename T, int KCH>
-__global__ void __launch_bounds__(512, 2) k_ysolve(Dev<T> D, int CW, int NCH)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    extern __shared__ unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);
-    T *sB = sA + CW * NCH;
-    const int t = threadIdx.x;
-    const int c = t % CW, k = t / CW;
-    const int i = blockIdx.x * CW + c;
-    const int nx = D.nx, ny = D.ny;
-    const bool col = i < nx;
-    const int j0 = k * KCH;
-    T r[KCH], m[KCH], e[KCH];
-    T A = (T)1, B = (T)0;
-#pragma unroll
-    for (int q = 0; q < KCH; q++) {
-        int j = j0 + q;
-        bool v = col && j < ny;
-        long long o = v ? fidx(D, i, j) : 0;
-        T rr = v ? D.dV[o] : (T)0;
-        if (v && j == 0) rr += D.corrS[i];
-        if (v && j == ny - 1) rr += D.corrN[i];
-        T mm = v ? D.fym[o] : (T)0;
-        T ee = v ? D.fye[o] : (T)1;
-        r[q] = rr; m[q] = mm; e[q] = ee;
-        B = mm * rr + ee * B;
-        A = ee * A;
-    }
-    // inclusive scan over the chunks of the column (earlier chunks first)
-    sA[t] = A; sB[t] = B;
-    for (int s = 1; s < NCH; s <<= 1) {
-        __syncthreads();
-        T Ap = (T)1, Bp = (T)0;
-        bool has = k >= s;
-        if (has) { Ap = sA[t - s * CW]; Bp = sB[t - s * CW]; }
-        __syncthreads();
-        if (has) { B = A * Bp + B; A = A * Ap; }
-        sA[t] = A; sB[t] = B;
-    }
-    __syncthreads();
-    T y = k > 0 ? sB[t - CW] : (T)0;
-    __syncthreads();
-    T cp[KCH];
-    T al = (T)0, be = (T)1;
-#pragma unroll
-    for (int q = 0; q < KCH; q++) {
-        int j = j0 + q;
-        bool v = col && j < ny;
-        y = m[q] * r[q] + e[q] * y;
-        r[q] = y;  // r now holds y
-        T cc = v ? D.fyc[fidx(D, i, v ? j : 0)] : (T)0;
-        cp[q] = cc;
-        al = al + be * y;
-        be = -cc * be;
-    }
-    // inclusive scan from the last chunk backwards: X_k = al_k + be_k X_{k+1}
-    sA[t] = al; sB[t] = be;
-    for (int s = 1; s < NCH; s <<= 1) {
-        __syncthreads();
-        T ap = (T)0, bp = (T)1;
-        bool has = k + s < NCH;
-        if (has) { ap = sA[t + s * CW]; bp = sB[t + s * CW]; }
-        __syncthreads();
-        if (has) { al = al + be * ap; be = be * bp; }
-        sA[t] = al; sB[t] = be;
-    }
-    __syncthreads();
-    T x = k + 1 < NCH ? sA[t + CW] : (T)0;
-    if (!col) return;
-#pragma unroll
-    for (int q = KCH - 1; q >= 0; q--) {
-        int j = j0 + q;
-        if (j < ny) {
-            x = r[q] - cp[q] * x;
-            long long o = fidx(D, i, j);
-            T Qo = D.Q[o], Qn, cn = (T)0;
-            if (D.kahan) {
-                T cq = D.cQ[o];
-                T yy = x - cq;
-                Qn = Qo + yy;
-                cn = (Qn - Qo) - yy;
-            } else {
-                Qn = Qo + x;
-            }
-            T gm = D.gx[i] * D.gy[j];
-            if (gm < (T)1) { Qn *= gm; cn *= gm; }
-            D.Q[o] = Qn;
-            if (D.kahan) D.cQ[o] = cn;
-        }
-    }
-}
-
-// ------------------------------------------------------------------ y-line solves, split
-
 // Three launches instead of one block scan: (A) every (column, chunk of KY
 // rows) summarises its chunk -- the forward elimination y_j = m_j r_j + e_j y_{j-1}
 // as y_end = A y_in + B, and the back substitution x_j = y_j - c'_j x_{j+1} as
@@ -1839,6 +1495,72 @@ __global__ void __launch_bounds__(256) k_ysum(Dev<T> D, int nch, T *sums)
     ysum_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, sums);
 }
 
+// A column of more than 32 CPL chunks: the warp passes over segments of 32 CPL
+// chunks, forward with the carried y, then backward with the carried x; the
+// y entering each chunk goes to yin on the forward pass and is read back by
+// the same lane on the backward pass.  sums, yin, xaft point at the column.
+template <typename T, int CPL>
+__device__ __noinline__ void yscan_long(int nch, const T *sums, long long s, T *yin, T *xaft, int lane)
+{
+    const int nseg = (nch + 32 * CPL - 1) / (32 * CPL);
+    T carry = (T)0;
+    for (int g = 0; g < nseg; g++) {
+        const int c0 = g * 32 * CPL + lane * CPL;
+        T a_[CPL], b_[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+            const bool v = c0 + q < nch;
+            a_[q] = v ? sums[c0 + q] : (T)1;
+            b_[q] = v ? sums[s + c0 + q] : (T)0;
+        }
+        T A = (T)1, B = (T)0;
+#pragma unroll
+        for (int q = 0; q < CPL; q++) { B = a_[q] * B + b_[q]; A = a_[q] * A; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
+        }
+        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) { Ae = (T)1; Be = (T)0; }
+        T y = Ae * carry + Be;
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+            if (c0 + q < nch) yin[c0 + q] = y;
+            y = a_[q] * y + b_[q];
+        }
+        carry = __shfl_sync(0xffffffffu, y, 31);
+    }
+    carry = (T)0;
+    for (int g = nseg - 1; g >= 0; g--) {
+        const int c0 = g * 32 * CPL + lane * CPL;
+        T a_[CPL], b_[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+            const bool v = c0 + q < nch;
+            a_[q] = v ? sums[2 * s + c0 + q] + sums[3 * s + c0 + q] * yin[c0 + q] : (T)0;
+            b_[q] = v ? sums[4 * s + c0 + q] : (T)1;
+        }
+        T al = (T)0, bb = (T)1;
+#pragma unroll
+        for (int q = CPL - 1; q >= 0; q--) { al = a_[q] + b_[q] * al; bb = b_[q] * bb; }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T ap = __shfl_down_sync(0xffffffffu, al, o), bp = __shfl_down_sync(0xffffffffu, bb, o);
+            if (lane + o < 32) { al = al + bb * ap; bb = bb * bp; }
+        }
+        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, bb, 1);
+        if (lane == 31) { an = (T)0; bn = (T)1; }
+        T x = an + bn * carry;
+#pragma unroll
+        for (int q = CPL - 1; q >= 0; q--) {
+            if (c0 + q < nch) xaft[c0 + q] = x;
+            x = a_[q] + b_[q] * x;
+        }
+        carry = __shfl_sync(0xffffffffu, x, 0);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void yscan_body(const Dev<T> &D, int blk, int nch, const T *sums, T *yin, T *xaft)
 {
@@ -1850,7 +1572,11 @@ __device__ __forceinline__ void yscan_body(const Dev<T> &D, int blk, int nch, co
     if (i >= nx) return;
     const int ns = ychunk_stride(nch);
     const long long s = (long long)nx * ns, base = (long long)i * ns;
-    constexpr int CPL = 8;  // chunks per lane (nch <= 256)
+    constexpr int CPL = 8;  // chunks per lane: 256 chunks per pass of the warp
+    if (nch > 32 * CPL) {
+        yscan_long<T, CPL>(nch, sums + base, s, yin + base, xaft + base, lane);
+        return;
+    }
     // all five summaries of the lane's chunks are loaded up front, as vectors
     // (the per-column stride is a multiple of 8 chunks); chunks past nch are
     // replaced by identities
@@ -2264,273 +1990,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
-// Same arithmetic as k_xsolve; the row's 13 input arrays are staged in shared
-// memory by bulk asynchronous copies issued by one thread, so the whole row's
-// loads are in flight at once.  Staged: dU, m, e, c', P, cP, w (interior
-// span) and Q, bC at rows j-1, j, j+1 (interior span plus one 16-byte halo
-// on each side).
+// Staging of the persistent x-solver: the row's input arrays dU, m, e, c', P,
+// cP, w (interior span) and Q, bC at rows j-1, j, j+1 (interior span plus one
+// 16-byte halo on each side) in shared memory.
 constexpr int XT_ARR_PLAIN = 7, XT_ARR_HALO = 6;
-
-template <typename T, int K>
-__global__ void __launch_bounds__(512) k_xsolve_tma(Dev<T> D, int span, double forced_dt_next)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar;
-    __shared__ T sA[32], sB[32];
-    __shared__ double smax[32];
-    const int hx = D.hx;
-    const int hspan = span + 2 * hx;  // halo arrays: columns -hx .. span+hx-1
-    T *S = reinterpret_cast<T *>(smem_raw);
-    T *sdU = S, *sm = S + span, *se = S + 2 * span, *sc = S + 3 * span, *sP = S + 4 * span;
-    T *scP = S + 5 * span, *sw = S + 6 * span;
-    T *sH = S + 7 * span;  // Q(j), Q(j-1), Q(j+1), bC(j), bC(j-1), bC(j+1), each hspan long
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
-    const int j = blockIdx.x;
-    const int nx = D.nx;
-    const long long rowo = fidx(D, 0, j);
-    const bool seq = D.cross_mode != 0;
-    T *wrow = D.w[cf.wc ^ 1] + rowo;
-    if (t == 0) {
-        mbar_init(&bar, 1);
-        fence_barrier_init();
-        const unsigned pb = (unsigned)(span * sizeof(T)), hb = (unsigned)(hspan * sizeof(T));
-        unsigned total = 6u * pb + (D.kahan ? pb : 0u) + (seq ? 6u * hb : 0u);
-        mbar_expect_tx(&bar, total);
-        tma_load_1d(sdU, D.dU + rowo, pb, &bar);
-        tma_load_1d(sm, D.fxm + rowo, pb, &bar);
-        tma_load_1d(se, D.fxe + rowo, pb, &bar);
-        tma_load_1d(sc, D.fxc + rowo, pb, &bar);
-        tma_load_1d(sP, D.P + rowo, pb, &bar);
-        if (D.kahan) tma_load_1d(scP, D.cP + rowo, pb, &bar);
-        tma_load_1d(sw, wrow, pb, &bar);
-        if (seq) {
-            const T *Qr = D.Q + rowo - hx, *br = D.bC + rowo - hx;
-            tma_load_1d(sH + 0 * hspan, Qr, hb, &bar);
-            tma_load_1d(sH + 1 * hspan, Qr - D.pitch, hb, &bar);
-            tma_load_1d(sH + 2 * hspan, Qr + D.pitch, hb, &bar);
-            tma_load_1d(sH + 3 * hspan, br, hb, &bar);
-            tma_load_1d(sH + 4 * hspan, br - D.pitch, hb, &bar);
-            tma_load_1d(sH + 5 * hspan, br + D.pitch, hb, &bar);
-        }
-    }
-    __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0, 1LL << 24);
-    if (__syncthreads_or(!ok)) {
-        // copies did not complete: flag it, wait once more (bounded) so no
-        // copy still targets this block's shared memory, and give up; the
-        // controller of the next step sees the flag and stops the run
-        mbar_wait_bounded(&bar, 0, 1LL << 24);
-        if (t == 0) {
-            atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
-            next_step_controller(D, 0.0, gridDim.x);
-        }
-        return;
-    }
-    if (seq) {
-        // Q^{n+1} ghosts at t_{n+1} where the staged rows need them: columns -1
-        // and nx of rows j-1, j, j+1 (W/E rule), then the whole ghost row when
-        // row j-1 or j+1 lies outside (S/N rule, applied to the filled row)
-        T *qrow[3] = {sH + 1 * hspan + hx, sH + 0 * hspan + hx, sH + 2 * hspan + hx};
-        if (t < 3) {
-            const int rr = j - 1 + t;
-            if (rr >= 0 && rr < D.ny) {
-                T *row = qrow[t];
-                row[-1] = D.bc[SW] == MAKER ? D.mqW[rr] : row[0];
-                row[nx] = D.bc[SE] == MAKER ? D.mqE[rr] : row[nx - 1];
-            }
-        }
-        __syncthreads();
-        if (j == 0 || j == D.ny - 1) {
-            const int side = j == 0 ? SS : SN;
-            const int gr = j == 0 ? -1 : D.ny;
-            T *dst = j == 0 ? qrow[0] : qrow[2];
-            const T *src = qrow[1];
-            const T *mq = side == SS ? D.mqS : D.mqN;  // maker Q at t_{n+1}, columns -1..nx
-            for (int c = t - 1; c <= nx; c += blockDim.x) dst[c] = D.bc[side] == MAKER ? mq[c + 1] : -src[c];
-            (void)gr;
-        }
-        __syncthreads();
-    }
-    if (!seq) {
-        // Q and bC of row j are still needed by the epilogue
-        const T *Qr = D.Q + rowo, *br = D.bC + rowo;
-        for (int q = t; q < span; q += blockDim.x) {
-            sH[0 * hspan + hx + q] = Qr[q];
-            sH[3 * hspan + hx + q] = br[q];
-        }
-        __syncthreads();
-    }
-    const int ib = t * K;
-    T r[K], m[K], e[K];
-#pragma unroll
-    for (int q = 0; q < K; q += VecT<T>::N) {
-        vload(sdU + ib + q, r + q);
-        vload(sm + ib + q, m + q);
-        vload(se + ib + q, e + q);
-    }
-    // row j of Q and bC (with one neighbour each side) stay in registers for
-    // the epilogue; all shared-memory reads are 16-byte vectors
-    T Qc[K + 2], bc_[K + 2];
-    load_halo_chunk<T, K>(sH + 0 * hspan + hx, ib, lane, Qc);
-    load_halo_chunk<T, K>(sH + 3 * hspan + hx, ib, lane, bc_);
-    if (seq) {
-        const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
-        const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
-        T qm[K + 2], qp[K + 2], bm[K], bp[K];
-        load_halo_chunk<T, K>(sH + 1 * hspan + hx, ib, lane, qm);
-        load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
-        vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
-        vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
-#pragma unroll
-        for (int q = 0; q < K; q++) {
-            T d = tmax(D.w_s - bc_[q + 1], (T)0);
-            T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
-            T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
-            T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
-            T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
-            T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
-            r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
-        }
-    }
-    const T corrW = D.corrW[j], corrE = D.corrE[j];
-#pragma unroll
-    for (int q = 0; q < K; q++) {
-        int i = ib + q;
-        if (i == 0) r[q] += corrW;
-        if (i == nx - 1) r[q] += corrE;
-        if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; }
-    }
-    T A = (T)1, B = (T)0;
-#pragma unroll
-    for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T Ap = __shfl_up_sync(0xffffffffu, A, o);
-        T Bp = __shfl_up_sync(0xffffffffu, B, o);
-        if (lane >= o) { B = A * Bp + B; A = A * Ap; }
-    }
-    if (lane == 31) { sA[wid] = A; sB[wid] = B; }
-    T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-    if (lane == 0) { Ae = (T)1; Be = (T)0; }
-    __syncthreads();
-    if (wid == 0) {
-        T a = lane < nw ? sA[lane] : (T)1, b = lane < nw ? sB[lane] : (T)0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T ap = __shfl_up_sync(0xffffffffu, a, o);
-            T bp = __shfl_up_sync(0xffffffffu, b, o);
-            if (lane >= o) { b = a * bp + b; a = a * ap; }
-        }
-        T bx = __shfl_up_sync(0xffffffffu, b, 1);
-        if (lane == 0) bx = (T)0;
-        if (lane < nw) sB[lane] = bx;
-    }
-    __syncthreads();
-    T y = Ae * sB[wid] + Be;
-#pragma unroll
-    for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
-    __syncthreads();
-    T c[K];
-#pragma unroll
-    for (int q = 0; q < K; q += VecT<T>::N) vload(sc + ib + q, c + q);
-#pragma unroll
-    for (int q = 0; q < K; q++)
-        if (ib + q >= nx) c[q] = (T)0;
-    T al = (T)0, be = (T)1;
-#pragma unroll
-    for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T ap = __shfl_down_sync(0xffffffffu, al, o);
-        T bp = __shfl_down_sync(0xffffffffu, be, o);
-        if (lane + o < 32) { al = al + be * ap; be = be * bp; }
-    }
-    if (lane == 0) { sA[wid] = al; sB[wid] = be; }
-    T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
-    if (lane == 31) { an = (T)0; bn = (T)1; }
-    __syncthreads();
-    if (wid == 0) {
-        T a = lane < nw ? sA[lane] : (T)0, b = lane < nw ? sB[lane] : (T)1;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T ap = __shfl_down_sync(0xffffffffu, a, o);
-            T bp = __shfl_down_sync(0xffffffffu, b, o);
-            if (lane + o < 32) { a = a + b * ap; b = b * bp; }
-        }
-        T ax = __shfl_down_sync(0xffffffffu, a, 1);
-        if (lane == 31) ax = (T)0;
-        if (lane < nw) sA[lane] = ax;
-    }
-    __syncthreads();
-    T x = an + bn * sA[wid];
-#pragma unroll
-    for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
-
-    T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo;
-    T Pv[K], cPv[K], wv[K];
-    const T *Qv = Qc + 1, *bv = bc_ + 1;
-#pragma unroll
-    for (int q = 0; q < K; q += VecT<T>::N) {
-        vload(sP + ib + q, Pv + q);
-        if (D.kahan) vload(scP + ib + q, cPv + q);
-        vload(sw + ib + q, wv + q);
-    }
-    const T gyj = D.gy[j];
-    T rate = (T)0;
-    bool bad = false;
-#pragma unroll
-    for (int q = 0; q < K; q++) {
-        const int i = ib + q;
-        if (i >= nx) continue;
-        T Pn, cn = (T)0;
-        if (D.kahan) {
-            T yy = r[q] - cPv[q];
-            Pn = Pv[q] + yy;
-            cn = (Pn - Pv[q]) - yy;
-        } else {
-            Pn = Pv[q] + r[q];
-        }
-        T wq = wv[q];
-        T gm = D.gx[i] * gyj;
-        if (gm < (T)1) {
-            T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
-            wq = bv[q] + (d + gm * (h - d));
-            wrow[i] = wq;
-            if (D.kahan) cwr[i] = (T)0;
-            Pn *= gm;
-            cn *= gm;
-        }
-        Pv[q] = Pn;
-        cPv[q] = cn;
-        T h = tmax(wq - bv[q], (T)0);
-        T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-        T u = iv * Pn, v = iv * Qv[q];
-        T cc = tsqrt(D.g * h);
-        rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
-        if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
-    }
-    vstore_k<T, K>(Pr + ib, Pv);
-    if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
-    double rr = (double)rate;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
-    bool anybad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) smax[wid] = anybad ? -1.0 : rr;
-    __syncthreads();
-    if (t == 0) {
-        double mx = 0.0;
-        bool fl = false;
-        for (int q = 0; q < nw; q++) {
-            if (smax[q] < 0.0) fl = true;
-            else mx = fmax(mx, smax[q]);
-        }
-        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
-        atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, forced_dt_next, gridDim.x);
-    }
-}
 
 // Issue the bulk copies of row j into one staging buffer (thread 0).
 template <typename T>
@@ -2786,286 +2249,6 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
         atomicMax(&D.ctl->rate_bits, dbits(mx));
         next_step_controller(D, forced_dt_next, gridDim.x);
-    }
-}
-
-// ---- two x-lines in flight per block
-//
-// The block's threads form two groups; each group solves its own rows
-// (blockIdx.x * 2 + g, stepping by 2 * gridDim.x) and synchronises on its own
-// named barrier, so one group's scans and epilogue overlap the other's.  The
-// inputs of the forward sweep (dU, m, e and the Q, bC rows j-1..j+1) are
-// staged per group by bulk copies into one buffer, refilled with the next row
-// as soon as the group has read it (at the first scan barrier); c', P, cP and
-// w go straight to registers.  Warp totals are composed by a shuffle scan
-// over the group's warps.  Same arithmetic as k_xsolve.
-constexpr int XG_ARR_PLAIN = 3, XG_ARR_HALO = 6;
-
-template <typename T>
-static size_t xgrp_smem(int span, int hx)
-{
-    return ((size_t)XG_ARR_PLAIN * span + (size_t)XG_ARR_HALO * (span + 2 * hx)) * sizeof(T);
-}
-
-__device__ __forceinline__ void named_sync(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-// barrier over `nthreads` threads that also ORs a predicate across them
-__device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
-{
-    unsigned r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((unsigned)pred), "r"(id), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
-template <typename T>
-__device__ __forceinline__ void xgrp_issue(const Dev<T> &D, int j, T *S, int span, unsigned long long *bar)
-{
-    const int hx = D.hx, hspan = span + 2 * hx;
-    const long long rowo = fidx(D, 0, j);
-    const bool seq = D.cross_mode != 0;
-    const unsigned pb = (unsigned)(span * sizeof(T)), hb = (unsigned)(hspan * sizeof(T));
-    mbar_expect_tx(bar, 3u * pb + 2u * hb + (seq ? 4u * hb : 0u));
-    tma_load_1d(S + 0 * span, D.dU + rowo, pb, bar);
-    tma_load_1d(S + 1 * span, D.fxm + rowo, pb, bar);
-    tma_load_1d(S + 2 * span, D.fxe + rowo, pb, bar);
-    T *sH = S + 3 * span;
-    const T *Qr = D.Q + rowo - hx, *br = D.bC + rowo - hx;
-    tma_load_1d(sH + 0 * hspan, Qr, hb, bar);
-    tma_load_1d(sH + 3 * hspan, br, hb, bar);
-    if (seq) {
-        tma_load_1d(sH + 1 * hspan, Qr - D.pitch, hb, bar);
-        tma_load_1d(sH + 2 * hspan, Qr + D.pitch, hb, bar);
-        tma_load_1d(sH + 4 * hspan, br - D.pitch, hb, bar);
-        tma_load_1d(sH + 5 * hspan, br + D.pitch, hb, bar);
-    }
-}
-
-template <typename T, int K>
-__global__ void __launch_bounds__(512, 1) k_xsolve_grp(Dev<T> D, int span, double forced_dt_next)
-{
-    const Coef cf = *D.coef;
-    if (!cf.active) return;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar[2];
-    __shared__ T sA[2][32], sB[2][32], sC[2][32], sD[2][32];
-    __shared__ double smax[32];
-    const int hx = D.hx, hspan = span + 2 * hx;
-    const int gthr = (int)blockDim.x >> 1;
-    const int t = threadIdx.x, g = t >= gthr ? 1 : 0, tg = t - g * gthr;
-    const int lane = t & 31, wid = tg >> 5, nwg = gthr >> 5, nw = (int)blockDim.x >> 5;
-    T *S = reinterpret_cast<T *>(smem_raw) + (size_t)g * ((size_t)XG_ARR_PLAIN * span + (size_t)XG_ARR_HALO * hspan);
-    const int nx = D.nx, ny = D.ny;
-    const bool seq = D.cross_mode != 0;
-    const int ib = tg * K;
-    const int j0 = (int)blockIdx.x * 2 + g, jstep = (int)gridDim.x * 2;
-    unsigned long long *bg = &bar[g];
-    if (tg == 0) {
-        mbar_init(bg, 1);
-        fence_barrier_init();
-        if (j0 < ny) xgrp_issue(D, j0, S, span, bg);
-    }
-    named_sync(1 + g, gthr);
-    T rate = (T)0;
-    bool bad = false, failed = false;
-    int it = 0;
-    T *wnew = D.w[cf.wc ^ 1];
-    for (int j = j0; j < ny; j += jstep, it++) {
-        const bool ok = mbar_wait_bounded(bg, (unsigned)(it & 1), 1LL << 24);
-        const long long rowo = fidx(D, 0, j);
-        T *sH = S + 3 * span;
-        T r[K], m[K], e[K];
-        vload_k<T, K>(S + ib, r);
-        vload_k<T, K>(S + span + ib, m);
-        vload_k<T, K>(S + 2 * span + ib, e);
-        T Qc[K + 2], bc_[K + 2];
-        load_halo_chunk<T, K>(sH + 0 * hspan + hx, ib, lane, Qc);
-        load_halo_chunk<T, K>(sH + 3 * hspan + hx, ib, lane, bc_);
-        if (seq) {
-            const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
-            const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
-            T qm[K + 2], qp[K + 2], bm[K], bp[K];
-            load_halo_chunk<T, K>(sH + 1 * hspan + hx, ib, lane, qm);
-            load_halo_chunk<T, K>(sH + 2 * hspan + hx, ib, lane, qp);
-            vload_k<T, K>(sH + 4 * hspan + hx + ib, bm);
-            vload_k<T, K>(sH + 5 * hspan + hx + ib, bp);
-            // ghosts of Q^{n+1} at t_{n+1}, as in k_xsolve_pipe
-            if (ib == 0) {
-                if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
-                Qc[0] = D.bc[SW] == MAKER ? D.mqW[j] : Qc[1];
-                if (j + 1 < ny) qp[0] = D.bc[SW] == MAKER ? D.mqW[j + 1] : qp[1];
-            }
-            if (nx - 1 >= ib && nx - 1 < ib + K) {
-                const int qe = nx - ib;
-#pragma unroll
-                for (int q = 1; q <= K; q++)
-                    if (q == qe) {
-                        if (j - 1 >= 0) qm[q + 1] = D.bc[SE] == MAKER ? D.mqE[j - 1] : qm[q];
-                        Qc[q + 1] = D.bc[SE] == MAKER ? D.mqE[j] : Qc[q];
-                        if (j + 1 < ny) qp[q + 1] = D.bc[SE] == MAKER ? D.mqE[j + 1] : qp[q];
-                    }
-            }
-            if (j == 0 || j == ny - 1) {
-                const int side = j == 0 ? SS : SN;
-                const T *mq = side == SS ? D.mqS : D.mqN;
-#pragma unroll
-                for (int q = 0; q < K + 2; q++) {
-                    const int cc = ib - 1 + q;
-                    const T gv = D.bc[side] == MAKER ? mq[min(max(cc, -1), nx) + 1] : -Qc[q];
-                    if (j == 0) qm[q] = gv;  // (no pointer select: keeps both arrays in registers)
-                    else qp[q] = gv;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < K; q++) {
-                T d = tmax(D.w_s - bc_[q + 1], (T)0);
-                T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
-                T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
-                T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
-                T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
-                T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
-                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
-            }
-        }
-        // operands of the back substitution and the epilogue, from memory
-        T c[K], Pv[K], cPv[K], wv[K];
-        vload_k<T, K>(D.fxc + rowo + ib, c);
-        vload_k<T, K>(D.P + rowo + ib, Pv);
-        if (D.kahan) vload_k<T, K>(D.cP + rowo + ib, cPv);
-        vload_k<T, K>(wnew + rowo + ib, wv);
-        const T corrW = D.corrW[j], corrE = D.corrE[j];
-#pragma unroll
-        for (int q = 0; q < K; q++) {
-            int i = ib + q;
-            if (i == 0) r[q] += corrW;
-            if (i == nx - 1) r[q] += corrE;
-            if (i >= nx) { r[q] = (T)0; m[q] = (T)0; e[q] = (T)1; c[q] = (T)0; }
-        }
-        T A = (T)1, B = (T)0;
-#pragma unroll
-        for (int q = 0; q < K; q++) { B = m[q] * r[q] + e[q] * B; A = e[q] * A; }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T Ap = __shfl_up_sync(0xffffffffu, A, o);
-            T Bp = __shfl_up_sync(0xffffffffu, B, o);
-            if (lane >= o) { B = A * Bp + B; A = A * Ap; }
-        }
-        if (lane == 31) { sA[g][wid] = A; sB[g][wid] = B; }
-        T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-        if (lane == 0) { Ae = (T)1; Be = (T)0; }
-        if (named_sync_or(1 + g, gthr, !ok)) { failed = true; break; }
-        // every thread of the group has read the staged row: refill it
-        if (tg == 0 && j + jstep < ny) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            xgrp_issue(D, j + jstep, S, span, bg);
-        }
-        // y entering this warp: inclusive scan of the group's warp totals
-        T qa = (T)1, qb = (T)0;
-        if (lane < nwg) { qa = sA[g][lane]; qb = sB[g][lane]; }
-        for (int o = 1; o < nwg; o <<= 1) {
-            T pa = __shfl_up_sync(0xffffffffu, qa, o);
-            T pb = __shfl_up_sync(0xffffffffu, qb, o);
-            if (lane >= o) { qb = qa * pb + qb; qa = qa * pa; }
-        }
-        T yw = __shfl_sync(0xffffffffu, qb, (wid + 31) & 31);
-        if (wid == 0) yw = (T)0;
-        T y = Ae * yw + Be;
-#pragma unroll
-        for (int q = 0; q < K; q++) { y = m[q] * r[q] + e[q] * y; r[q] = (ib + q < nx) ? y : (T)0; }
-        T al = (T)0, be = (T)1;
-#pragma unroll
-        for (int q = K - 1; q >= 0; q--) { al = r[q] - c[q] * al; be = -c[q] * be; }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T ap = __shfl_down_sync(0xffffffffu, al, o);
-            T bp = __shfl_down_sync(0xffffffffu, be, o);
-            if (lane + o < 32) { al = al + be * ap; be = be * bp; }
-        }
-        if (lane == 0) { sC[g][wid] = al; sD[g][wid] = be; }
-        T an = __shfl_down_sync(0xffffffffu, al, 1), bn = __shfl_down_sync(0xffffffffu, be, 1);
-        if (lane == 31) { an = (T)0; bn = (T)1; }
-        named_sync(1 + g, gthr);
-        // x just after this warp: suffix scan of the group's warp totals
-        T qc = (T)0, qd = (T)1;
-        if (lane < nwg) { qc = sC[g][lane]; qd = sD[g][lane]; }
-        for (int o = 1; o < nwg; o <<= 1) {
-            T pc = __shfl_down_sync(0xffffffffu, qc, o);
-            T pd = __shfl_down_sync(0xffffffffu, qd, o);
-            if (lane + o < 32) { qc = qc + qd * pc; qd = qd * pd; }
-        }
-        T xw = __shfl_sync(0xffffffffu, qc, (wid + 1) & 31);
-        if (wid == nwg - 1) xw = (T)0;
-        T x = an + bn * xw;
-#pragma unroll
-        for (int q = K - 1; q >= 0; q--) { x = r[q] - c[q] * x; r[q] = x; }
-
-        T *Pr = D.P + rowo, *cPr = D.cP + rowo, *cwr = D.cw + rowo, *wrow = wnew + rowo;
-        const T *Qv = Qc + 1, *bv = bc_ + 1;
-        const T gyj = D.gy[j];
-#pragma unroll
-        for (int q = 0; q < K; q++) {
-            const int i = ib + q;
-            if (i >= nx) continue;
-            T Pn, cn = (T)0;
-            if (D.kahan) {
-                T yy = r[q] - cPv[q];
-                Pn = Pv[q] + yy;
-                cn = (Pn - Pv[q]) - yy;
-            } else {
-                Pn = Pv[q] + r[q];
-            }
-            T wq = wv[q];
-            T gm = D.gx[i] * gyj;
-            if (gm < (T)1) {
-                T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
-                wq = bv[q] + (d + gm * (h - d));
-                wrow[i] = wq;
-                if (D.kahan) cwr[i] = (T)0;
-                Pn *= gm;
-                cn *= gm;
-            }
-            Pv[q] = Pn;
-            cPv[q] = cn;
-            T h = tmax(wq - bv[q], (T)0);
-            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-            T u = iv * Pn, v = iv * Qv[q];
-            T cc = tsqrt(D.g * h);
-            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
-            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
-        }
-        if (ib < nx) {
-            vstore_k<T, K>(Pr + ib, Pv);
-            if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
-        }
-    }
-    if (failed) {
-        // copies did not complete: wait (bounded) for what is in flight and
-        // let the controller of the next step stop the run
-        mbar_wait_bounded(bg, (unsigned)(it & 1), 1LL << 22);
-    }
-    __syncthreads();
-    double rr = (double)rate;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
-    bool anybad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) smax[t >> 5] = anybad ? -1.0 : rr;
-    const bool anyfailed = __syncthreads_or(failed);
-    if (t == 0) {
-        double mx = 0.0;
-        bool fl = false;
-        for (int q = 0; q < nw; q++) {
-            if (smax[q] < 0.0) fl = true;
-            else mx = fmax(mx, smax[q]);
-        }
-        if (anyfailed) atomicOr(&D.ctl->err, ERR_DEVICE_WAIT);
-        if (fl) atomicOr(&D.ctl->err, ERR_NONFINITE);
-        atomicMax(&D.ctl->rate_bits, dbits(mx));
-        next_step_controller(D, anyfailed ? 0.0 : forced_dt_next, gridDim.x);
     }
 }
 
@@ -3592,18 +2775,6 @@ __global__ void k_set_limits(Ctl *ctl, double t_end, long long max_steps)
 
 // ------------------------------------------------------------------ launchers
 
-// y-solver shape: chunk length kch, chunks per column NCH, columns per block CW
-template <typename T>
-static void ysolve_shape(const Dev<T> &D, int &CW, int &NCH, int &kch)
-{
-    kch = D.tune_ykch > 0 ? D.tune_ykch : (sizeof(T) == 4 ? 16 : 8);
-    while (kch < 32 && (D.ny + kch - 1) / kch > 512) kch *= 2;
-    NCH = (D.ny + kch - 1) / kch;
-    int maxthr = D.tune_ythreads > 0 ? min(D.tune_ythreads, 512) : 512;
-    CW = 32;
-    while (CW > 1 && CW * NCH > maxthr) CW >>= 1;
-}
-
 template <typename T>
 static int ysplit_rows(int tune)
 {
@@ -3620,9 +2791,10 @@ int ysplit_chunks(int ny, int tune)
 template <typename T>
 int step_shape_ok(int nx, int ny)
 {
-    // y-solver: block scan over at most 512 chunks of 32 rows (the split
-    // y-solver takes over up to 256 chunks); x-solver: at most 512 threads of 32
-    return (ny + 31) / 32 <= 512 && nx <= 512 * 32;
+    // x-solver: at most 512 threads of 32 elements a row; y-solver: any
+    // number of chunks (the chunk scan loops over segments of 256 chunks)
+    (void)ny;
+    return nx <= 512 * 32;
 }
 
 // x-solver chunk: elements per thread (a multiple of the vector width), at
@@ -3644,34 +2816,20 @@ int row_pitch(int nx, int tune)
     return ((nx + span - 1) / span) * span + span;
 }
 
-constexpr size_t XTMA_MAX_SMEM = 200 * 1024;
 constexpr size_t XPIPE_MAX_SMEM = 220 * 1024;
 
 template <typename T>
 cudaError_t configure(int nx)
 {
     (void)nx;
-    const int bytes = (int)XTMA_MAX_SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_xsolve_tma<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_tma<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_tma<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_tma<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     const int pb = (int)XPIPE_MAX_SMEM;
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_pipe<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    cudaError_t e = cudaFuncSetAttribute(k_xsolve_pipe<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_pipe<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_pipe<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_pipe<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_grp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_xsolve_grp<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_xsolve_warp<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (e == cudaSuccess)
@@ -3701,22 +2859,13 @@ static bool launch_rhs2(const Dev<float> &D, cudaStream_t st, int rows, int ky)
 static bool launch_rhs2(const Dev<double> &, cudaStream_t, int, int) { return false; }
 
 // x-solver variants (tune_xtma): 0 automatic -- in single precision the
-// warp-per-row kernel where its shared-memory rows fit, else the two-group
-// kernel where a row takes at most 256 threads of K = 4 or 8 elements and
-// both staging buffers fit; then the one-row persistent kernel, else the
-// per-row staged kernel, else registers only; 1 registers only; 2 the
-// two-group kernel where it fits; 3 the one-row persistent kernel; 4 the
+// warp-per-row kernel where its shared-memory rows fit, else the persistent
+// kernel with two staged rows where they fit, else registers only; in double
+// precision the persistent kernel where it fits, else registers only;
+// 1 registers only; 3 the persistent kernel where it fits; 4 the
 // warp-per-row kernel where it fits.
 template <typename T>
-static bool xsolver_grouped(const Dev<T> &D, int nx)
-{
-    const int K = x_chunk<T>(nx, D.tune_xk);
-    const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
-    const bool want = D.tune_xtma == 2 || (D.tune_xtma == 0 && sizeof(T) == 4);
-    return want && (K == 4 || K == 8) && thr <= 256 && 2 * xgrp_smem<T>(thr * K, D.hx) <= XPIPE_MAX_SMEM;
-}
-template <typename T>
-static bool xsolver_staging_allowed(const Dev<T> &D)
+static bool xsolver_pipe_allowed(const Dev<T> &D)
 {
     return D.tune_xtma == 0 || D.tune_xtma == 3;
 }
@@ -3741,7 +2890,7 @@ static bool rhs_fast(const Dev<T> &D)
 template <typename T>
 static bool rhs_pair(const Dev<T> &D)
 {
-    return sizeof(T) == 4 && D.tune_rhs != 1 && D.tune_rhs1 == 0 && D.tune_rows != 16 && D.theta == (T)1 &&
+    return sizeof(T) == 4 && D.tune_rhs1 == 0 && D.tune_rows != 16 && D.theta == (T)1 &&
            D.cross_mode != 0 && D.kahan != 0 && D.fstride * 15 < 0x7fffffffLL;
 }
 // Rows per warp of the sliding-window RHS kernels.  A warp walks its strip's
@@ -3783,7 +2932,7 @@ static bool rhs_fuses_ysum(const Dev<T> &D)
 {
     const int rows = rhs_rows(D);
     const bool pair_fuses = rhs_pair(D) && rows % ysplit_rows<T>(D.tune_yk) == 0;  // bands start on chunks
-    return D.tune_rhs != 1 && (pair_fuses || (rhs_fast(D) && rows != 16)) && D.ysplit && D.tune_ysum == 0;
+    return (pair_fuses || (rhs_fast(D) && rows != 16)) && D.tune_ysum == 0;
 }
 
 // Dynamic shared memory of the ghost kernels: the single-precision maker's
@@ -3805,52 +2954,44 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     const int nx = D.nx, ny = D.ny;
     long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
     int gb = (int)((nwork + 255) / 256);
-    bool ysum_fused = false;  // the RHS kernel forms the y-line chunk summaries
     if (ev) cudaEventRecord(ev[0], st);
     k_ghost<T><<<gb, 256, ghost_smem(D), st>>>(D);
     if (ev) cudaEventRecord(ev[1], st);
-    if (D.tune_rhs == 1) {
-        constexpr int TX = 32, TY = 8;
-        dim3 g1((nx + TX - 1) / TX, (ny + TY - 1) / TY);
-        k_rhs_combine<T, TX, TY><<<g1, dim3(TX, TY), 0, st>>>(D);
-    } else {
-        const int rows = rhs_rows(D);
-        const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
-        const int nband = (ny + rows - 1) / rows;
-        const long long nwarp = (long long)nstrip * nband;
-        const int blocks = (int)((nwarp + 3) / 4);
-        const bool fast = rhs_fast(D);
-        ysum_fused = rhs_fuses_ysum(D);
-        const bool t1 = D.theta == (T)1;
-        const bool pair2 = rhs_pair(D);
-        if (pair2) {
-            launch_rhs2(D, st, rows, ysum_fused ? ysplit_rows<T>(D.tune_yk) : 0);
-        } else if (fast && ysum_fused) {
-            const int KY = ysplit_rows<T>(D.tune_yk);
-            if (rows == 32) {
-                if (KY == 16) k_rhs_sw<T, 32, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
-                else k_rhs_sw<T, 32, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
-            } else {
-                if (KY == 16) k_rhs_sw<T, 64, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
-                else k_rhs_sw<T, 64, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
-            }
-        } else if (fast) {
-            if (rows == 16) k_rhs_sw<T, 16, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
-            else if (rows == 32) k_rhs_sw<T, 32, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 64, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
-        } else if (rows == 16) {
-            if (t1) k_rhs_sw<T, 16, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 16, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
-        } else if (rows == 64) {
-            if (t1) k_rhs_sw<T, 64, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 64, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
+    const int rows = rhs_rows(D);
+    const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
+    const int nband = (ny + rows - 1) / rows;
+    const long long nwarp = (long long)nstrip * nband;
+    const int blocks = (int)((nwarp + 3) / 4);
+    const bool fast = rhs_fast(D);
+    const bool ysum_fused = rhs_fuses_ysum(D);  // the RHS kernel forms the y-line chunk summaries
+    const bool t1 = D.theta == (T)1;
+    if (rhs_pair(D)) {
+        launch_rhs2(D, st, rows, ysum_fused ? ysplit_rows<T>(D.tune_yk) : 0);
+    } else if (fast && ysum_fused) {
+        const int KY = ysplit_rows<T>(D.tune_yk);
+        if (rows == 32) {
+            if (KY == 16) k_rhs_sw<T, 32, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 32, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
         } else {
-            if (t1) k_rhs_sw<T, 32, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
-            else k_rhs_sw<T, 32, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
+            if (KY == 16) k_rhs_sw<T, 64, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
+            else k_rhs_sw<T, 64, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
         }
+    } else if (fast) {
+        if (rows == 16) k_rhs_sw<T, 16, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+        else if (rows == 32) k_rhs_sw<T, 32, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw<T, 64, true, true><<<blocks, 128, 0, st>>>(D, nstrip);
+    } else if (rows == 16) {
+        if (t1) k_rhs_sw<T, 16, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw<T, 16, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
+    } else if (rows == 64) {
+        if (t1) k_rhs_sw<T, 64, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw<T, 64, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
+    } else {
+        if (t1) k_rhs_sw<T, 32, true, false><<<blocks, 128, 0, st>>>(D, nstrip);
+        else k_rhs_sw<T, 32, false, false><<<blocks, 128, 0, st>>>(D, nstrip);
     }
     if (ev) cudaEventRecord(ev[2], st);
-    if (D.ysplit) {
+    {
         const int KY = ysplit_rows<T>(D.tune_yk);
         const int nch = (ny + KY - 1) / KY;
         dim3 gb2((nx + 31) / 32, (nch + 7) / 8);
@@ -3864,14 +3005,6 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         const dim3 gw((nx + 255) / 256, nch);
         if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
         else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
-    } else {
-        int CW, NCH, kch;
-        ysolve_shape<T>(D, CW, NCH, kch);
-        size_t sm = 2 * (size_t)CW * NCH * sizeof(T);
-        dim3 gy((nx + CW - 1) / CW);
-        if (kch == 32) k_ysolve<T, 32><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
-        else if (kch == 8) k_ysolve<T, 8><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
-        else k_ysolve<T, 16><<<gy, CW * NCH, sm, st>>>(D, CW, NCH);
     }
     if (ev) cudaEventRecord(ev[3], st);
     const int K = x_chunk<T>(nx, D.tune_xk);
@@ -3879,10 +3012,8 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     const int span = thr * K;
     const size_t xs = xtma_smem<T>(span, D.hx);
     const bool xwarp = xsolver_warp(D, nx);
-    const bool grp = !xwarp && xsolver_grouped(D, nx);
-    const bool pipe = !grp && xsolver_staging_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM;
-    const bool tma = xwarp || grp || pipe || (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
-    if (D.cross_mode != 0 && !tma) {
+    const bool pipe = !xwarp && xsolver_pipe_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM;
+    if (D.cross_mode != 0 && !xwarp && !pipe) {
         long long ng = 4LL * ny + 4LL * (nx + 4);
         k_ghost_q<T><<<(int)((ng + 255) / 256), 256, ghost_smem(D), st>>>(D);
     }
@@ -3899,22 +3030,12 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
             if (fixed) k_xsolve_warp<T, 8, true><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
             else k_xsolve_warp<T, 8><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
         }
-    } else if (grp) {
-        const int grid = min((ny + 1) / 2, D.nsm);
-        const size_t gs = 2 * xgrp_smem<T>(span, D.hx);
-        if (K == 4) k_xsolve_grp<T, 4><<<grid, 2 * thr, gs, st>>>(D, span, forced_dt_next);
-        else k_xsolve_grp<T, 8><<<grid, 2 * thr, gs, st>>>(D, span, forced_dt_next);
     } else if (pipe) {
         const int grid = min(ny, D.nsm);
         if (K == 4) k_xsolve_pipe<T, 4><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
         else if (K == 8) k_xsolve_pipe<T, 8><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
         else if (K == 16) k_xsolve_pipe<T, 16><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
         else k_xsolve_pipe<T, 32><<<grid, thr, 2 * xs, st>>>(D, span, forced_dt_next);
-    } else if (tma) {
-        if (K == 4) k_xsolve_tma<T, 4><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
-        else if (K == 8) k_xsolve_tma<T, 8><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
-        else if (K == 16) k_xsolve_tma<T, 16><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
-        else k_xsolve_tma<T, 32><<<ny, thr, xs, st>>>(D, span, forced_dt_next);
     } else if (K == 4) k_xsolve<T, 4><<<ny, thr, 0, st>>>(D, forced_dt_next);
     else if (K == 8) k_xsolve<T, 8><<<ny, thr, 0, st>>>(D, forced_dt_next);
     else if (K == 16) k_xsolve<T, 16><<<ny, thr, 0, st>>>(D, forced_dt_next);
@@ -3923,15 +3044,14 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     return cudaGetLastError();
 }
 
-// 1 when the x-solver stages rows in shared memory (and patches Q ghosts there)
+// 1 when the x-solver patches the Q ghosts itself (no k_ghost_q launch)
 template <typename T>
 int xsolver_staged(const Dev<T> &D, int nx)
 {
     const int K = x_chunk<T>(nx, D.tune_xk);
     const int thr = ((nx + K - 1) / K + 31) / 32 * 32;
     const size_t xs = xtma_smem<T>(thr * K, D.hx);
-    return xsolver_warp(D, nx) || xsolver_grouped(D, nx) ||
-           (xsolver_staging_allowed(D) && xs <= XTMA_MAX_SMEM);
+    return xsolver_warp(D, nx) || (xsolver_pipe_allowed(D) && 2 * xs <= XPIPE_MAX_SMEM);
 }
 
 // kernel launches of one step, by the decisions step_impl takes
@@ -3940,7 +3060,7 @@ int step_launches(const Dev<T> &D)
 {
     const int nx = D.nx;
     const bool ghost_q = D.cross_mode != 0 && !xsolver_staged(D, nx);
-    const int ylaunch = D.ysplit ? (rhs_fuses_ysum(D) ? 2 : 3) : 1;
+    const int ylaunch = rhs_fuses_ysum(D) ? 2 : 3;
     return 1 /* ghost */ + 1 /* rhs */ + ylaunch + (ghost_q ? 1 : 0) + 1 /* x-solver */;
 }
 
