@@ -68,6 +68,8 @@ __device__ __forceinline__ T gslope(T qm, T q0, T qp, T th)
 
 // 1 / sqrt(h^4 + max(h^4, eps)) of the desingularised velocity of KP07,
 // u = sqrt(2) h m / sqrt(h^4 + max(h^4, eps))
+#define BSQ_SQRT2 1.41421356237309504880
+
 template <typename T>
 __device__ __forceinline__ T desing_inv(T h, T eps)
 {
@@ -76,7 +78,34 @@ __device__ __forceinline__ T desing_inv(T h, T eps)
     return trsqrt(h4 + tmax(h4, eps));
 }
 
-#define BSQ_SQRT2 1.41421356237309504880
+// Desingularised velocity factor and celerity of a depth h (KP07, Sec. 3.4):
+// iv = sqrt(2) h / sqrt(h^4 + max(h^4, eps)), so u = iv P, v = iv Q, and
+// c = sqrt(g h).  Single precision evaluates them as written.  Double
+// precision, whose square roots and divisions are long instruction sequences
+// at GB300's FP64 rate, takes both from one reciprocal square root r of h
+// where h^4 >= eps: there iv = 1/h exactly, so iv = r^2 and c = sqrt(g) h r;
+// the near-dry side (h^4 < eps) keeps the formula.
+template <typename T>
+struct IvC {
+    T iv, c;
+};
+__device__ __forceinline__ IvC<float> ivc(float h, float g, float sqrtg, float eps)
+{
+    (void)sqrtg;
+    return {(float)BSQ_SQRT2 * h * desing_inv(h, eps), sqrtf(g * h)};
+}
+__device__ __forceinline__ IvC<double> ivc(double h, double g, double sqrtg, double eps)
+{
+    (void)g;
+    const double h2 = h * h, h4 = h2 * h2;
+    const double r = rsqrt(fmax(h, 1e-300));
+    IvC<double> o;
+    o.c = sqrtg * h * r;
+    o.iv = r * r;
+    if (h4 < eps) o.iv = BSQ_SQRT2 * h * rsqrt(h4 + eps);
+    return o;
+}
+
 
 // vector loads and stores of K contiguous elements (float4 / double2)
 template <typename T> struct VecT;
@@ -739,14 +768,14 @@ __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
 
 template <typename T>
-__device__ __forceinline__ FaceSt<T> face_state(T wf, T Pf, T Qf, T bf, T g, T eps)
+__device__ __forceinline__ FaceSt<T> face_state(T wf, T Pf, T Qf, T bf, T g, T sqrtg, T eps)
 {
     FaceSt<T> s;
     s.h = tmax(wf - bf, (T)0);
-    T iv = (T)BSQ_SQRT2 * s.h * desing_inv(s.h, eps);
-    s.u = iv * Pf;
-    s.v = iv * Qf;
-    s.c = tsqrt(g * s.h);
+    const IvC<T> ic = ivc(s.h, g, sqrtg, eps);
+    s.u = ic.iv * Pf;
+    s.v = ic.iv * Qf;
+    s.c = ic.c;
     return s;
 }
 
@@ -810,7 +839,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     const int kc = min(i, nx + 2), kc1 = min(i + 1, nx + 2);
     const bool lane_out = lane >= 2 && lane <= 29 && i < nx;
     const T *w = D.w[cf.wc];
-    const T g = D.g, eps = D.eps, th = THETA1 ? (T)1 : D.theta;
+    const T g = D.g, eps = D.eps, th = THETA1 ? (T)1 : D.theta, sqrtg = tsqrt(g);
     const T rdx = D.rdx, rdy = D.rdy, half_rdx = (T)0.5 * rdx, half_rdy = (T)0.5 * rdy;
     const T rdx2 = rdx * rdx, rdy2 = rdy * rdy, q_rdxy = (T)0.25 * rdx * rdy;
     const T c_xxx = (T)0.5 * rdx2 * rdx, c_yyy = (T)0.5 * rdy2 * rdy;
@@ -914,8 +943,8 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
             T wl, wh, Pl, Ph, Ql, Qh;
             reconstruct(wW[1], wW[2], wW[3], PW[1], PW[2], PW[3], QW[1], QW[2], QW[3], bS, bN, th,
                         wl, wh, Pl, Ph, Ql, Qh);
-            FaceSt<T> S = face_state(wl, Pl, Ql, bS, g, eps);
-            FaceSt<T> Nn = face_state(wh, Ph, Qh, bN, g, eps);
+            FaceSt<T> S = face_state(wl, Pl, Ql, bS, g, sqrtg, eps);
+            FaceSt<T> Nn = face_state(wh, Ph, Qh, bN, g, sqrtg, eps);
             T h0, h1, h2;
             cu_flux_st<T, 1>(Nprev, S, g, h0, h1, h2);  // face (r-1)-1/2 = o+1/2 for o = r-2
             // ---- finish row o = r - 2
@@ -927,8 +956,8 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
             T bxW = (T)0.5 * (KW[0] + KW[1]), bxE = (T)0.5 * (KRW[0] + KRW[1]);
             T xwl, xwh, xPl, xPh, xQl, xQh;
             reconstruct(wm, w0, wp, Pm, P0, Pp, Qm, Q0, Qp, bxW, bxE, th, xwl, xwh, xPl, xPh, xQl, xQh);
-            FaceSt<T> Wst = face_state(xwl, xPl, xQl, bxW, g, eps);
-            FaceSt<T> Est = face_state(xwh, xPh, xQh, bxE, g, eps);
+            FaceSt<T> Wst = face_state(xwl, xPl, xQl, bxW, g, sqrtg, eps);
+            FaceSt<T> Est = face_state(xwh, xPh, xQh, bxE, g, sqrtg, eps);
             FaceSt<T> El;  // E state of the lane to the left
             El.h = shup(Est.h, 1); El.u = shup(Est.u, 1); El.v = shup(Est.v, 1); El.c = shup(Est.c, 1);
             T x0, x1, x2;
@@ -1958,9 +1987,9 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         Pv[q] = Pn;
         cPv[q] = cn;
         T h = tmax(wq - bv[q], (T)0);
-        T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-        T u = iv * Pn, v = iv * Qv[q];
-        T cc = tsqrt(D.g * h);
+        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+        T u = ic.iv * Pn, v = ic.iv * Qv[q];
+        T cc = ic.c;
         rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
         if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
     }
@@ -2252,9 +2281,9 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             Pv[q] = Pn;
             cPv[q] = cn;
             T h = tmax(wq - bv[q], (T)0);
-            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-            T u = iv * Pn, v = iv * Qv[q];
-            T cc = tsqrt(D.g * h);
+            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+            T u = ic.iv * Pn, v = ic.iv * Qv[q];
+            T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
             if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
         }
@@ -2490,9 +2519,9 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             Pv[q] = Pn;
             cPv[q] = cn;
             T h = tmax(wq - bv[q], (T)0);
-            T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-            T u = iv * Pn, v = iv * Qv[q];
-            T cc = tsqrt(D.g * h);
+            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+            T u = ic.iv * Pn, v = ic.iv * Qv[q];
+            T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
             if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
         }
@@ -2786,9 +2815,9 @@ __global__ void __launch_bounds__(256) k_rate(Dev<T> D, int wc)
         int i = (int)(q % D.nx), j = (int)(q / D.nx);
         long long c = fidx(D, i, j);
         T h = tmax(w[c] - D.bC[c], (T)0);
-        T iv = (T)BSQ_SQRT2 * h * desing_inv(h, D.eps);
-        T u = iv * D.P[c], v = iv * D.Q[c];
-        T cc = tsqrt(D.g * h);
+        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+        T u = ic.iv * D.P[c], v = ic.iv * D.Q[c];
+        T cc = ic.c;
         T r = tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy);
         mx = fmax(mx, (double)r);
     }
