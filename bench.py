@@ -133,8 +133,9 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, interval_s=0.001):
         self.index = index
+        self.interval_s = interval_s
         self.p = None
         self.nv = None
         self.samples = []
@@ -145,7 +146,7 @@ class Clocks:
             smp = self.nv.sample()
             if smp is not None:
                 self.samples.append(smp)
-            time.sleep(0.001)
+            time.sleep(self.interval_s)
 
     def __enter__(self):
         import threading
@@ -424,7 +425,7 @@ def run_ours(args):
             "kernel_ms": kms,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches * args.steps + 2,
+            "gpu_launches": launches * args.steps + 1,
             "launches_per_step": launches,
             "fp64": fp64,
             "batched": batched,
@@ -601,7 +602,10 @@ def run_served(args, dev, stream):
     t0 = time.perf_counter()
     submitted, ids, done_at, steps, failed = 0, {}, {}, {}, 0
     h2d = d2h = 0
-    max_running = 0
+    max_running = max_pending = 0
+    max_bytes = 0
+    held_by_budget = held_by_slots = polls = 0  # polls that ended with requests still queued
+    timeline, next_sample, area, last = [], 0.0, 0.0, 0.0
     while len(done_at) < n:
         now = time.perf_counter() - t0
         while submitted < n and arrivals[submitted] <= now:
@@ -612,7 +616,22 @@ def run_served(args, dev, stream):
                         + sum(c[k].size for k in ("eta0", "P0", "Q0") if c.get(k) is not None))
             submitted += 1
         nr, npd = srv.poll()
+        polls += 1
         max_running = max(max_running, nr)
+        max_pending = max(max_pending, npd)
+        used = srv.bytes_in_use()
+        max_bytes = max(max_bytes, used)
+        if npd > 0:
+            if nr < args.serve_slots:
+                held_by_budget += 1
+            else:
+                held_by_slots += 1
+        now = time.perf_counter() - t0
+        area += npd * (now - last)
+        last = now
+        if now >= next_sample:
+            timeline.append([round(now, 2), nr, npd, round(used / 1e9, 3)])
+            next_sample = now + args.serve_sample_s
         for rid, q in list(ids.items()):
             r = srv.request(rid)
             if r["state"] in (bsq.REQ_DONE, bsq.REQ_FAILED):
@@ -642,8 +661,26 @@ def run_served(args, dev, stream):
         "value": work / makespan, "unit": "cell-updates/s",
         "offered": work / max(arrivals[-1] - arrivals[0], 1e-9),
         "makespan_s": makespan, "cell_updates": work, "failed": failed, "max_running": max_running,
+        "max_pending": max_pending, "mean_pending": area / max(last, 1e-9), "max_bytes_in_use": max_bytes,
+        "polls": polls, "polls_held_by_budget": held_by_budget, "polls_held_by_slots": held_by_slots,
+        "timeline_t_running_pending_gb": timeline,
         "e2e_bytes": {"h2d": h2d, "d2h": d2h},
     }
+
+
+def run_served_only(args):
+    """The served workload alone (one GPU, rank 0): one JSON line with the
+    served figures."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    with Clocks(0, interval_s=0.05) as ck:
+        served = run_served(args, dev, stream)
+    line = {"metric": "served time-to-result and cell-updates/s", "served": served, "clocks": ck.summary()}
+    print(json.dumps(line))
+    return 0
 
 
 def run_fixed_vs_adaptive(args, dev, stream):
@@ -741,6 +778,10 @@ def main(argv=None):
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-round", type=int, default=32)
+    ap.add_argument("--serve-sample-s", type=float, default=0.25, help="queue timeline sampling interval")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the configured served workload: 256 requests, full durations U[5, 60] s, 8 GB budget "
+                         "(about two minutes of GPU time); reported alone")
     ap.add_argument("--batch-domains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-solo-steps", type=int, default=32)
@@ -753,6 +794,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.oracle_worker:
         return oracle_worker(args)
+    if args.serve_full:
+        args.serve_requests, args.serve_time_scale, args.serve_budget_gb = 256, 1.0, 8.0
+        args.serve_sample_s = max(args.serve_sample_s, 1.0)
+        return run_served_only(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

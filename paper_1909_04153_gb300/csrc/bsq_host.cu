@@ -45,7 +45,9 @@ struct bsq_domain {
     Dev<float> Df;
     Dev<double> Dd;
     cudaGraphExec_t graph;
+    cudaGraphExec_t part[8];  // graphs of 1, 2, 4, ... steps below graph_steps (remainders)
     int graph_steps;
+    int ctl_fresh;            // h_ctl equals the device Ctl (no work enqueued since it was read)
     bsq_status sticky;
     int n_state_fields;  // fields saved by a checkpoint
 };
@@ -494,6 +496,8 @@ extern "C" void bsq_destroy(bsq_domain *d)
     if (!d) return;
     if (d->stream) cudaStreamSynchronize(d->stream);
     if (d->graph) cudaGraphExecDestroy(d->graph);
+    for (int k = 0; k < 8; k++)
+        if (d->part[k]) cudaGraphExecDestroy(d->part[k]);
     if (d->dmem) cudaFree(d->dmem);
     if (d->h_ctl) cudaFreeHost(d->h_ctl);
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
@@ -516,10 +520,8 @@ static cudaError_t enqueue_step(bsq_domain *d, double forced_dt_next)
 // that step size).
 static cudaError_t enqueue_start(bsq_domain *d, double t_end, long long max_steps, double forced_dt)
 {
-    cudaError_t e = launch_set_limits(d->ctl, d->stream, t_end, max_steps);
-    if (e != cudaSuccess) return e;
-    return d->fp64 ? launch_prologue<double>(d->Dd, d->stream, forced_dt)
-                   : launch_prologue<float>(d->Df, d->stream, forced_dt);
+    return d->fp64 ? launch_prologue<double>(d->Dd, d->stream, forced_dt, t_end, max_steps)
+                   : launch_prologue<float>(d->Df, d->stream, forced_dt, t_end, max_steps);
 }
 
 static bsq_status read_ctl(const bsq_domain *d)
@@ -536,18 +538,43 @@ static bsq_status ctl_status(const Ctl &c)
     return BSQ_OK;
 }
 
-static bsq_status build_graph(bsq_domain *d)
+// Capture `steps` steps into an executable graph.
+static bsq_status capture_steps(bsq_domain *d, int steps, cudaGraphExec_t *out)
 {
-    if (d->graph) return BSQ_OK;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int s = 0; s < d->graph_steps && e == cudaSuccess; s++) e = enqueue_step(d, 0.0);
+    for (int s = 0; s < steps && e == cudaSuccess; s++) e = enqueue_step(d, 0.0);
     cudaError_t e2 = cudaStreamEndCapture(d->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) return BSQ_ERR_CUDA;
-    e = cudaGraphInstantiate(&d->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { d->graph = nullptr; return BSQ_ERR_CUDA; }
+    if (e != cudaSuccess) { *out = nullptr; return BSQ_ERR_CUDA; }
+    return BSQ_OK;
+}
+
+// The graph of graph_steps steps and the remainder graphs of 1, 2, 4, ...
+// steps below it (any remainder is at most a handful of graph launches).
+static bsq_status build_graph(bsq_domain *d)
+{
+    if (d->graph) return BSQ_OK;
+    bsq_status st = capture_steps(d, d->graph_steps, &d->graph);
+    for (int k = 0; k < 8 && st == BSQ_OK && (1 << k) < d->graph_steps; k++)
+        st = capture_steps(d, 1 << k, &d->part[k]);
+    return st;
+}
+
+// Enqueue m step slots: whole graphs, then the remainder as its binary parts.
+static bsq_status enqueue_slots(bsq_domain *d, long long m)
+{
+    for (long long r = 0; r < m / d->graph_steps; r++)
+        if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return BSQ_ERR_CUDA;
+    const long long rem = m % d->graph_steps;
+    for (int k = 7; k >= 0; k--)
+        if (rem & (1LL << k)) {
+            cudaError_t e = d->part[k] ? cudaGraphLaunch(d->part[k], d->stream) : cudaErrorInvalidValue;
+            if (e != cudaSuccess) return BSQ_ERR_CUDA;
+        }
     return BSQ_OK;
 }
 
@@ -581,25 +608,28 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
     if (!d) return BSQ_ERR_ARG;
     if (d->sticky != BSQ_OK) return d->sticky;
     if (isnan(t_end) || (max_steps <= 0 && !isfinite(t_end))) return BSQ_ERR_ARG;
-    bsq_status st = read_ctl(d);
-    if (st != BSQ_OK) return set_sticky(d, st);
+    bsq_status st = BSQ_OK;
+    if (!d->ctl_fresh) {  // (a call that ended with the controller state read needs no second read)
+        st = read_ctl(d);
+        if (st != BSQ_OK) return set_sticky(d, st);
+    }
     const long long n0 = d->h_ctl->n;
     st = build_graph(d);
     if (st != BSQ_OK) return set_sticky(d, st);
+    d->ctl_fresh = 0;
     if (cudaSuccess != enqueue_start(d, t_end, max_steps, 0.0)) return set_sticky(d, BSQ_ERR_CUDA);
-    // Whole graphs of graph_steps steps, then the remainder as single steps,
-    // so a call runs exactly the step slots it may need: max_steps of them,
-    // or about the steps left to t_end (slots past the end do no work).
+    // Whole graphs of graph_steps steps, then the remainder in graphs of 1, 2,
+    // 4, ... steps, so a call runs exactly the step slots it may need:
+    // max_steps of them, or about the steps left to t_end (slots past the end
+    // do no work).
     const double tol = isfinite(t_end) ? 1e-12 * fmax(1.0, fabs(t_end)) : 0.0;
     long long budget = max_steps > 0 ? max_steps : LLONG_MAX;
     int grow = 1;
     for (;;) {
         const long long est = steps_left_estimate(d->h_ctl->t, t_end, d->h_ctl->last_dt);
         const long long m = steps_to_enqueue(budget, est, d->graph_steps, grow);
-        for (long long r = 0; r < m / d->graph_steps; r++)
-            if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
-        for (long long r = 0; r < m % d->graph_steps; r++)
-            if (enqueue_step(d, 0.0) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+        st = enqueue_slots(d, m);
+        if (st != BSQ_OK) return set_sticky(d, st);
         if (budget != LLONG_MAX) budget -= m;
         st = read_ctl(d);
         if (st != BSQ_OK) return set_sticky(d, st);
@@ -609,6 +639,7 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
         if (grow < 64) grow *= 2;
     }
     if (steps_done) *steps_done = d->h_ctl->n - n0;
+    d->ctl_fresh = 1;
     return set_sticky(d, st);
 }
 
@@ -620,6 +651,7 @@ extern "C" bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n)
     for (long long q = 0; q < n; q++)
         if (!(dts[q] > 0.0) || !isfinite(dts[q])) return BSQ_ERR_ARG;
     if (n == 0) return BSQ_OK;
+    d->ctl_fresh = 0;
     if (cudaSuccess != enqueue_start(d, INFINITY, 0, dts[0])) return set_sticky(d, BSQ_ERR_CUDA);
     for (long long q = 0; q < n; q++) {
         if (enqueue_step(d, q + 1 < n ? dts[q + 1] : 0.0) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
@@ -632,6 +664,7 @@ extern "C" bsq_status bsq_step_dt(bsq_domain *d, const double *dts, long long n)
     }
     bsq_status st = read_ctl(d);
     if (st != BSQ_OK) return set_sticky(d, st);
+    d->ctl_fresh = 1;
     return set_sticky(d, ctl_status(*d->h_ctl));
 }
 
@@ -925,6 +958,7 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
     }
     for (int d = 0; d < n; d++) {
         if (b->doms[d]->sticky != BSQ_OK) return b->doms[d]->sticky;
+        b->doms[d]->ctl_fresh = 0;
         bsq_status s = wait_stream(b->doms[d]);  // the domain's own work comes first
         if (s != BSQ_OK) return set_sticky(b->doms[d], s);
     }
@@ -1010,6 +1044,7 @@ extern "C" bsq_status bsq_batch_advance(bsq_batch *b, const double *t_end, long 
     for (int d = 0; d < n; d++) {
         if (steps_done) steps_done[d] = b->h_ctl[d].n - n0[d];
         *b->doms[d]->h_ctl = b->h_ctl[d];
+        b->doms[d]->ctl_fresh = 1;
         bsq_status s = ctl_status(b->h_ctl[d]);
         if (s != BSQ_OK) {
             set_sticky(b->doms[d], s);
@@ -1219,6 +1254,7 @@ extern "C" bsq_status bsq_restore(bsq_domain *d, const void *buf, size_t len)
     const char *o = (const char *)buf + sizeof(h);
     bsq_status st = wait_stream(d);
     if (st != BSQ_OK) return st;
+    d->ctl_fresh = 0;
     CK(cudaMemcpy(d->ctl, o, sizeof(Ctl), cudaMemcpyHostToDevice));
     o += sizeof(Ctl);
     for (void *p : ptrs) {
@@ -1279,6 +1315,7 @@ extern "C" bsq_status bsq_profile_kernels(bsq_domain *d, long long n_steps, doub
         if (cudaEventCreate(&ev[k]) != cudaSuccess) return BSQ_ERR_CUDA;
     for (int k = 0; k < 5; k++) ms_out[k] = 0.0;
     bsq_status st = BSQ_OK;
+    d->ctl_fresh = 0;
     if (cudaSuccess != enqueue_start(d, INFINITY, n_steps, 0.0)) st = BSQ_ERR_CUDA;
     for (long long q = 0; q < n_steps && st == BSQ_OK; q++) {
         cudaError_t e = d->fp64 ? launch_step_timed<double>(d->Dd, d->stream, 0.0, ev)

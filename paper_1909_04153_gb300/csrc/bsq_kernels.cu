@@ -497,8 +497,11 @@ __device__ void controller(const Dev<T> &D, double forced_dt, Coef &cf, unsigned
 
 // Controller for the step about to start (one thread); forced_dt > 0 replays a step size.
 template <typename T>
-__global__ void k_prologue(Dev<T> D, double forced_dt)
+__global__ void k_prologue(Dev<T> D, double forced_dt, double t_end, long long max_steps)
 {
+    // limits of the run, then the controller of its first step
+    D.ctl->t_end = t_end;
+    D.ctl->n_limit = max_steps > 0 ? D.ctl->n + max_steps : 0x7fffffffffffffffLL;
     Coef cf;
     unsigned err;
     controller(D, forced_dt, cf, err);
@@ -2877,12 +2880,6 @@ __global__ void __launch_bounds__(256) k_mass(Dev<T> D, int wc, double *partial)
     }
 }
 
-__global__ void k_set_limits(Ctl *ctl, double t_end, long long max_steps)
-{
-    ctl->t_end = t_end;
-    ctl->n_limit = max_steps > 0 ? ctl->n + max_steps : 0x7fffffffffffffffLL;
-}
-
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
@@ -3175,9 +3172,9 @@ int step_launches(const Dev<T> &D)
 }
 
 template <typename T>
-cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt)
+cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt, double t_end, long long max_steps)
 {
-    k_prologue<T><<<1, 1, 0, st>>>(D, forced_dt);
+    k_prologue<T><<<1, 1, 0, st>>>(D, forced_dt, t_end, max_steps);
     return cudaGetLastError();
 }
 
@@ -3215,12 +3212,6 @@ template <typename T>
 cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks)
 {
     k_mass<T><<<nblocks, 256, 0, st>>>(D, wc, partial);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long max_steps)
-{
-    k_set_limits<<<1, 1, 0, st>>>(ctl, t_end, max_steps);
     return cudaGetLastError();
 }
 
@@ -3440,7 +3431,7 @@ cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t 
     template cudaError_t launch_rate<T>(const Dev<T> &, cudaStream_t, int);                      \
     template cudaError_t launch_setup<T>(const Dev<T> &, cudaStream_t, const SetupArgs &);       \
     template cudaError_t launch_maker_table<T>(const Dev<T> &, cudaStream_t);                    \
-    template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double);               \
+    template cudaError_t launch_prologue<T>(const Dev<T> &, cudaStream_t, double, double, long long); \
     template int xsolver_staged<T>(const Dev<T> &, int);                                         \
     template int step_launches<T>(const Dev<T> &);                                               \
     template int batch_xchunk<T>();                                                              \

@@ -17,13 +17,13 @@ template <typename T> cudaError_t launch_step(const Dev<T> &D, cudaStream_t st, 
 template <typename T> cudaError_t launch_step_timed(const Dev<T> &D, cudaStream_t st, double forced_dt, cudaEvent_t *ev);
 template <typename T> int xsolver_staged(const Dev<T> &D, int nx);
 template <typename T> int step_launches(const Dev<T> &D);
-template <typename T> cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt);
+template <typename T>
+cudaError_t launch_prologue(const Dev<T> &D, cudaStream_t st, double forced_dt, double t_end, long long max_steps);
 template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, int wc);
 template <typename T> cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A);
 template <typename T> cudaError_t launch_maker_table(const Dev<T> &D, cudaStream_t st);
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
 template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);
-cudaError_t launch_set_limits(Ctl *ctl, cudaStream_t st, double t_end, long long max_steps);
 cudaError_t launch_fma64(double *out, int blocks, int n, cudaStream_t st);  // 256 threads a block
 
 // batched steps over many domains (one launch per stage)
