@@ -136,11 +136,12 @@ bsq_status bsq_create(const bsq_params *p, const double *bed_corners, const bsq_
  * start of Sec. 3.2.1) until t = t_end (the last step is clamped to land on
  * t_end) or max_steps more steps were taken (<= 0: no limit; then t_end must
  * be finite).  *steps_done (may be NULL) receives the number taken.  Runs
- * captured CUDA graphs of graph_steps steps and single steps for the
- * remainder: with max_steps it enqueues exactly max_steps step slots, toward
- * t_end about the steps the last step size says are left, and slots past the
- * end do no work.  Errors: BSQ_ERR_ARG, BSQ_ERR_NONFINITE, BSQ_ERR_UNSTABLE,
- * BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
+ * captured CUDA graphs of graph_steps steps and graphs of 1, 2, 4, ... steps
+ * for the remainder (the domain's first call launches its steps one by one
+ * while it captures the graphs): with max_steps it enqueues exactly max_steps
+ * step slots, toward t_end about the steps the last step size says are left,
+ * and slots past the end do no work.  Errors: BSQ_ERR_ARG, BSQ_ERR_NONFINITE,
+ * BSQ_ERR_UNSTABLE, BSQ_ERR_TIMEOUT, BSQ_ERR_CUDA. */
 bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_steps, long long *steps_done);
 
 /* Take n steps with the given step sizes dts[0..n-1] (host array, each > 0 and

@@ -353,7 +353,7 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     dm->ctl = D.ctl;
     dm->coef = D.coef;
     dm->mass_partial = (double *)(base + o_mass);
-    // explicit y-solver shapes, or columns of more than 256 chunks, select the block-scan kernel
+    // y-line chunk summaries (5 per chunk) and the scanned values entering and leaving each chunk
     D.ysums = (T *)(base + o_ysum);
     D.yin = D.ysums + 5 * nchy;
     D.yxa = D.ysums + 6 * nchy;
@@ -614,8 +614,6 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
         if (st != BSQ_OK) return set_sticky(d, st);
     }
     const long long n0 = d->h_ctl->n;
-    st = build_graph(d);
-    if (st != BSQ_OK) return set_sticky(d, st);
     d->ctl_fresh = 0;
     if (cudaSuccess != enqueue_start(d, t_end, max_steps, 0.0)) return set_sticky(d, BSQ_ERR_CUDA);
     // Whole graphs of graph_steps steps, then the remainder in graphs of 1, 2,
@@ -628,7 +626,15 @@ extern "C" bsq_status bsq_advance(bsq_domain *d, double t_end, long long max_ste
     for (;;) {
         const long long est = steps_left_estimate(d->h_ctl->t, t_end, d->h_ctl->last_dt);
         const long long m = steps_to_enqueue(budget, est, d->graph_steps, grow);
-        st = enqueue_slots(d, m);
+        if (!d->graph) {
+            // the domain's first run: these steps launch one by one, and the
+            // graphs are captured and instantiated while the device runs them
+            for (long long r = 0; r < m; r++)
+                if (enqueue_step(d, 0.0) != cudaSuccess) return set_sticky(d, BSQ_ERR_CUDA);
+            st = build_graph(d);
+        } else {
+            st = enqueue_slots(d, m);
+        }
         if (st != BSQ_OK) return set_sticky(d, st);
         if (budget != LLONG_MAX) budget -= m;
         st = read_ctl(d);
@@ -1124,28 +1130,22 @@ extern "C" bsq_status bsq_read_device(const bsq_domain *d, int field, void *dev_
 extern "C" bsq_status bsq_read(const bsq_domain *d, int field, double *host_out)
 {
     if (!d || !host_out || field < 0 || field > 4) return BSQ_ERR_ARG;
-    size_t ncell = (size_t)d->nx * d->ny;
-    size_t esz = d->fp64 ? 8 : 4;
-    void *tmp = nullptr;
-    if (cudaMallocAsync(&tmp, ncell * esz, d->stream) != cudaSuccess) return BSQ_ERR_OOM;
-    bsq_status st = bsq_read_device(d, field, tmp);
-    std::vector<float> hf;
-    if (st == BSQ_OK) {
-        if (d->fp64) {
-            if (cudaMemcpyAsync(host_out, tmp, ncell * 8, cudaMemcpyDeviceToHost, d->stream) != cudaSuccess)
-                st = BSQ_ERR_CUDA;
-        } else {
-            hf.resize(ncell);
-            if (cudaMemcpyAsync(hf.data(), tmp, ncell * 4, cudaMemcpyDeviceToHost, d->stream) != cudaSuccess)
-                st = BSQ_ERR_CUDA;
-        }
-    }
+    if (d->sticky != BSQ_OK && d->sticky != BSQ_ERR_NONFINITE && d->sticky != BSQ_ERR_UNSTABLE)
+        return d->sticky;
+    const size_t ncell = (size_t)d->nx * d->ny;
+    bsq_status st = read_ctl(d);
+    if (st != BSQ_OK) return st;
+    const int wc = (int)(d->h_ctl->n & 1);
+    // widened to double on the device, then one copy into the caller's array
+    double *tmp = nullptr;
+    if (cudaMallocAsync((void **)&tmp, ncell * sizeof(double), d->stream) != cudaSuccess) return BSQ_ERR_OOM;
+    cudaError_t e = d->fp64 ? launch_extract_f64<double>(d->Dd, d->stream, wc, field, tmp)
+                            : launch_extract_f64<float>(d->Df, d->stream, wc, field, tmp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, ncell * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
     cudaFreeAsync(tmp, d->stream);
     bsq_status w = wait_stream(d);
-    if (st == BSQ_OK) st = w;
-    if (st == BSQ_OK && !d->fp64)
-        for (size_t q = 0; q < ncell; q++) host_out[q] = (double)hf[q];
-    return st;
+    if (e != cudaSuccess) return BSQ_ERR_CUDA;
+    return w;
 }
 
 extern "C" bsq_status bsq_info(const bsq_domain *d, double *t, long long *n, double *last_dt, double *mass,

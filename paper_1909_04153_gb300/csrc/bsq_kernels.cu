@@ -2644,58 +2644,49 @@ __global__ void k_setup_centres(Dev<T> D, SetupArgs A)
     }
 }
 
-// Eq. 21 coefficients of cell (i, j) along a line: a (previous), b (diagonal), c (next)
-__device__ __forceinline__ void eq21_coef(double d, double dm, double dp, double h, double kB, double &a, double &b,
-                                          double &c)
-{
-    const double gd = (dp - dm) / (2.0 * h);
-    a = d * gd / (6.0 * h) - kB * d * d / (h * h);
-    b = 1.0 + 2.0 * kB * d * d / (h * h);
-    c = -d * gd / (6.0 * h) - kB * d * d / (h * h);
-}
-
 // Thomas factors (m, -a m, c' = c m) of every x-line (one thread per row) and
 // y-line (one thread per column), boundary rows closed: wall or sponge = odd
 // mirror of the normal flux (the outside coefficient moves onto the diagonal),
-// maker = the outside value is known (its coefficient goes to cW..cN)
+// maker = the outside value is known (its coefficient goes to cW..cN).  The
+// rows of Eq. 21 come from the still depth with reciprocals of the cell size
+// taken once, so the only division of a step is its pivot's: the pivots form
+// a chain along the line, and with a few hundred lines on the device each
+// thread's chain of double-precision divisions is what the set-up waits on.
+// One warp per block spreads the lines over the multiprocessors.
 template <typename T>
-__global__ void k_setup_factors(Dev<T> D, SetupArgs A)
+__global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const double kB = A.Bd + 1.0 / 3.0;
     const int nx = D.nx, ny = D.ny;
-    if (t < ny) {
-        const int j = t;
-        double cprev = 0.0;
-        for (int i = 0; i < nx; i++) {
-            double a, b, c;
-            eq21_coef(A.dd[fidx(D, i, j)], A.dd[fidx(D, i - 1, j)], A.dd[fidx(D, i + 1, j)], A.dx, kB, a, b, c);
-            if (i == 0) { A.cW[j] = a; if (A.bt[0] != MAKER) b -= a; a = 0.0; }
-            if (i == nx - 1) { A.cE[j] = c; if (A.bt[1] != MAKER) b -= c; c = 0.0; }
-            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
-            const double m = 1.0 / (b - a * cprev);
-            cprev = c * m;
-            const long long o = fidx(D, i, j);
-            D.fxm[o] = (T)m;
-            D.fxe[o] = (T)(-a * m);
-            D.fxc[o] = (T)cprev;
-        }
-    } else if (t < ny + nx) {
-        const int i = t - ny;
-        double cprev = 0.0;
-        for (int j = 0; j < ny; j++) {
-            double a, b, c;
-            eq21_coef(A.dd[fidx(D, i, j)], A.dd[fidx(D, i, j - 1)], A.dd[fidx(D, i, j + 1)], A.dy, kB, a, b, c);
-            if (j == 0) { A.cS[i] = a; if (A.bt[2] != MAKER) b -= a; a = 0.0; }
-            if (j == ny - 1) { A.cN[i] = c; if (A.bt[3] != MAKER) b -= c; c = 0.0; }
-            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
-            const double m = 1.0 / (b - a * cprev);
-            cprev = c * m;
-            const long long o = fidx(D, i, j);
-            D.fym[o] = (T)m;
-            D.fye[o] = (T)(-a * m);
-            D.fyc[o] = (T)cprev;
-        }
+    const bool xline = t < ny;
+    if (!xline && t >= ny + nx) return;
+    const int n = xline ? nx : ny;
+    const double h = xline ? A.dx : A.dy;
+    const double r2h = 0.5 / h, r6h = 1.0 / (6.0 * h), rh2 = 1.0 / (h * h);
+    const int lo = xline ? A.bt[0] : A.bt[2], hi = xline ? A.bt[1] : A.bt[3];
+    double *cfirst = xline ? A.cW : A.cS, *clast = xline ? A.cE : A.cN;
+    T *fm = xline ? D.fxm : D.fym, *fe = xline ? D.fxe : D.fye, *fc = xline ? D.fxc : D.fyc;
+    const int line = xline ? t : t - ny;
+    auto at = [&](int k) { return xline ? fidx(D, k, line) : fidx(D, line, k); };
+    double dm = A.dd[at(-1)], d0 = A.dd[at(0)];
+    double cprev = 0.0;
+    for (int k = 0; k < n; k++) {
+        const double dp = A.dd[at(k + 1)];
+        const double gd = (dp - dm) * r2h;
+        const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
+        double a = t1 - t2, b = 1.0 + 2.0 * t2, c = -t1 - t2;
+        if (k == 0) { cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
+        if (k == n - 1) { clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
+        if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+        const double m = 1.0 / (b - a * cprev);
+        cprev = c * m;
+        const long long o = at(k);
+        fm[o] = (T)m;
+        fe[o] = (T)(-a * m);
+        fc[o] = (T)cprev;
+        dm = d0;
+        d0 = dp;
     }
 }
 
@@ -2732,7 +2723,7 @@ cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
     k_setup_fill<T><<<gs, 256, 0, st>>>(D);
     k_setup_corner<T><<<gs, 256, 0, st>>>(D, A);
     k_setup_centres<T><<<gs, 256, 0, st>>>(D, A);
-    k_setup_factors<T><<<(D.nx + D.ny + 127) / 128, 128, 0, st>>>(D, A);
+    k_setup_factors<T><<<(D.nx + D.ny + 31) / 32, 32, 0, st>>>(D, A);
     k_setup_state<T><<<gs, 256, 0, st>>>(D, A);
     return cudaGetLastError();
 }
@@ -2833,9 +2824,10 @@ __global__ void __launch_bounds__(256) k_rate(Dev<T> D, int wc)
     }
 }
 
-// Interior field into a compact nx*ny array of T.
-template <typename T>
-__global__ void __launch_bounds__(256) k_extract(Dev<T> D, int wc, int field, T *out)
+// Interior field into a compact nx*ny array of O (T, or double for reads
+// that widen on the device).
+template <typename T, typename O>
+__global__ void __launch_bounds__(256) k_extract(Dev<T> D, int wc, int field, O *out)
 {
     long long ncell = (long long)D.nx * D.ny;
     const T *w = D.w[wc];
@@ -2853,7 +2845,7 @@ __global__ void __launch_bounds__(256) k_extract(Dev<T> D, int wc, int field, T 
         case 3: v = h; break;
         default: v = w[c]; break;
         }
-        out[q] = v;
+        out[q] = (O)v;
     }
 }
 
@@ -3204,7 +3196,16 @@ cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, 
 {
     long long ncell = (long long)D.nx * D.ny;
     int gb = (int)std::min<long long>((ncell + 255) / 256, 4096);
-    k_extract<T><<<gb, 256, 0, st>>>(D, wc, field, out);
+    k_extract<T, T><<<gb, 256, 0, st>>>(D, wc, field, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_extract_f64(const Dev<T> &D, cudaStream_t st, int wc, int field, double *out)
+{
+    long long ncell = (long long)D.nx * D.ny;
+    int gb = (int)std::min<long long>((ncell + 255) / 256, 4096);
+    k_extract<T, double><<<gb, 256, 0, st>>>(D, wc, field, out);
     return cudaGetLastError();
 }
 
@@ -3440,6 +3441,7 @@ cudaError_t launch_batch_gather(const Dev<T> *Ds, int n, Ctl *out, cudaStream_t 
     template cudaError_t launch_batch_start<T>(const Dev<T> *, int, const double *, long long, cudaStream_t); \
     template cudaError_t launch_batch_gather<T>(const Dev<T> *, int, Ctl *, cudaStream_t);       \
     template cudaError_t launch_extract<T>(const Dev<T> &, cudaStream_t, int, int, T *);         \
+    template cudaError_t launch_extract_f64<T>(const Dev<T> &, cudaStream_t, int, int, double *); \
     template cudaError_t launch_mass<T>(const Dev<T> &, cudaStream_t, int, double *, int);
 BSQ_INST(float)
 BSQ_INST(double)

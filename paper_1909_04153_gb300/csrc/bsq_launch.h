@@ -23,6 +23,7 @@ template <typename T> cudaError_t launch_rate(const Dev<T> &D, cudaStream_t st, 
 template <typename T> cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A);
 template <typename T> cudaError_t launch_maker_table(const Dev<T> &D, cudaStream_t st);
 template <typename T> cudaError_t launch_extract(const Dev<T> &D, cudaStream_t st, int wc, int field, T *out);
+template <typename T> cudaError_t launch_extract_f64(const Dev<T> &D, cudaStream_t st, int wc, int field, double *out);
 template <typename T> cudaError_t launch_mass(const Dev<T> &D, cudaStream_t st, int wc, double *partial, int nblocks);
 cudaError_t launch_fma64(double *out, int blocks, int n, cudaStream_t st);  // 256 threads a block
 
