@@ -36,18 +36,26 @@ import numpy as np  # noqa: E402
 from paper_1909_04153_gb300 import workloads as W  # noqa: E402
 
 METRIC = "cell-updates/s"
-# floating-point operations of one cell-update, counted from the FP32 step
-# kernels' instruction mix (add, mul, 2 x fma) without halo recomputation
-FLOPS_PER_CELL = 420
+# floating-point operations of one double-precision cell-update (2 per DFMA,
+# 1 per DADD or DMUL) and FP64 instructions, counted with ncu
+# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum) on one
+# launch of each kernel of the double-precision step on the 2048 x 2048 barred
+# beach: RHS 513.1 flops (402 instructions), x-line solve 77.4, y-line solve
+# 10.8, ghost cells 0.1 (summarised under profiles/)
+FP64_FLOPS_PER_CELL = 601.5
+FP64_INSTR_PER_CELL = 472.0
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate, beside the rate measured live (bsq_fp64_fma_rate)
 # DRAM bytes per launch of the dominant kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (kernel, precision, nx, ny); the capture is summarised under profiles/
-MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.875968e6 + 113.007872e6}
-# algorithmic bytes per interior cell of each kernel (values it must read +
-# write once), per precision; the whole step in STEP_VALUES
-KERNEL_VALUES = {"fp32": {"rhs_combine": 21, "ysolve": 8, "xsolve": 11},
-                 "fp64": {"rhs_combine": 19, "ysolve": 6, "xsolve": 9}}
+MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.867264e6 + 113.133824e6}
+# algorithmic bytes per interior cell of each kernel (values the method needs it
+# to read and write once: state, bed, compensation terms, history; the
+# right-hand sides dU, dV of the line solves and the stored line factors are
+# this design's intermediates and are not counted), per precision; the whole
+# step in STEP_VALUES
+KERNEL_VALUES = {"fp32": {"rhs_combine": 19, "ysolve": 4, "xsolve": 7},
+                 "fp64": {"rhs_combine": 17, "ysolve": 2, "xsolve": 5}}
 STEP_VALUES = {"fp32": 25, "fp64": 19}
 
 
@@ -368,13 +376,17 @@ def run_ours(args):
         k64 = d64.profile_kernels(3)
         d64.close()
         v64 = ncell / (ms64 * 1e-3)
-        fl = FLOPS_PER_CELL * v64 / 1e12
+        fl = FP64_FLOPS_PER_CELL * v64 / 1e12
         fma64 = bsq.fp64_fma_rate()
+        # FP64 instructions issue at half the flop rate of fused multiply-adds
+        ins = FP64_INSTR_PER_CELL * v64 / 1e12
         fp64 = {"value": v64, "unit": "cell-updates/s", "ms_per_step": ms64, "steps": args.fp64_steps,
                 "kernel_ms": k64,
                 "roofline": {"bound": "alu", "achieved": fl, "peak": fma64, "unit": "TFLOP/s",
                              "frac": fl / fma64, "peak_kind": "measured (FP64 FMA chains, bsq_fp64_fma_rate)",
-                             "nominal_peak": FP64_PEAK_TFLOPS, "flops_per_cell": FLOPS_PER_CELL}}
+                             "nominal_peak": FP64_PEAK_TFLOPS, "flops_per_cell": FP64_FLOPS_PER_CELL,
+                             "fp64_instr_per_cell": FP64_INSTR_PER_CELL,
+                             "fp64_issue_frac": ins / (fma64 / 2.0)}}
 
     # end to end through the C ABI with host buffers: create (uploads the
     # bathymetry and initial state), advance, read eta back
