@@ -336,3 +336,54 @@ def test_fp32_maker_with_steps_above_a_25th_of_the_period():
         assert d.advance(t_end=dt * steps) == steps
         # FP32 resolves eta to ~1e-7 of the depth; the waves here are ~6e-4 m rms
         assert rel(d.read("eta"), o.get("eta")) <= 1e-3
+
+
+# ------------------------------------------------------------------ call boundaries
+
+def test_step_slots_are_exact_and_calls_compose():
+    # A call enqueues exactly its step slots (whole graphs of graph_steps,
+    # then graphs of 1, 2, 4, ... steps): 37 steps in one call, in calls of
+    # 16 + 21, in 37 single steps, and through bsq_step_dt with the same step
+    # sizes give bitwise the same state, time and step count.
+    case = W.barred_beach(nx=96, ny=72)
+    with bsq.Domain(case, precision="fp32", graph_steps=16) as a:
+        assert a.advance(max_steps=37) == 37
+        sa = {f: a.read(f) for f in ("eta", "P", "Q")}
+        ia = a.info()
+    with bsq.Domain(case, precision="fp32", graph_steps=16) as b:
+        assert b.advance(max_steps=16) == 16 and b.advance(max_steps=21) == 21
+        for f in ("eta", "P", "Q"):
+            np.testing.assert_array_equal(b.read(f), sa[f])
+        assert b.info()["t"] == ia["t"] and b.info()["n"] == 37
+    dts = []
+    with bsq.Domain(case, precision="fp32", graph_steps=16) as c:
+        for _ in range(37):
+            assert c.advance(max_steps=1) == 1
+            dts.append(c.info()["last_dt"])
+        for f in ("eta", "P", "Q"):
+            np.testing.assert_array_equal(c.read(f), sa[f])
+        assert c.info()["t"] == ia["t"]
+    with bsq.Domain(case, precision="fp32", graph_steps=16) as e:
+        e.step_dt(dts)
+        for f in ("eta", "P", "Q"):
+            np.testing.assert_array_equal(e.read(f), sa[f])
+
+
+def test_advance_to_t_end_after_restore_and_batch():
+    # the controller state a call starts from is read again whenever other work
+    # may have changed it: after a restore, and after a batched advance
+    case = W.random_basin(64, seed=31, forcing="jonswap")
+    with bsq.Domain(case, precision="fp32") as a, bsq.Domain(case, precision="fp32") as b:
+        a.advance(max_steps=10)
+        snap = a.checkpoint()
+        a.advance(max_steps=30)
+        a.restore(snap)
+        assert a.info()["n"] == 10
+        assert a.advance(max_steps=5) == 5 and a.info()["n"] == 15
+        with bsq.Batch([b]) as bt:
+            bt.advance(max_steps=12)
+        assert b.info()["n"] == 12
+        t_end = b.info()["t"] + 0.05
+        assert b.advance(t_end=t_end) >= 1
+        assert abs(b.info()["t"] - t_end) <= 1e-12 * max(1.0, t_end)
+        assert b.advance(max_steps=3) == 3 and b.info()["n"] > 15
