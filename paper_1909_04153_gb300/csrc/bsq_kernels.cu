@@ -336,6 +336,10 @@ __device__ MakerStep maker_step(const Dev<T> &D, double t, double t_next)
 // carry an L2 evict-last policy, so the table (a few megabytes, read every step)
 // tends to stay in L2 while the step's streaming kernels pass through.
 constexpr int MK_BATCH_ONE = 32, MK_BATCH_MANY = 16;
+// Makers of at most MK_FEW components take a kernel compiled with batches of
+// that size: the launch is a chain of latencies, and a fraction of the code
+// (fewer unrolled loads to fetch cold, fewer registers) shortens it.
+constexpr int MK_FEW = 4;
 
 __device__ __forceinline__ unsigned long long l2_keep_policy()
 {
@@ -696,10 +700,10 @@ __device__ __forceinline__ void ghost_body(const Dev<T> &D, long long first, lon
     }
 }
 
-template <typename T>
+template <typename T, int MB = MK_BATCH_ONE>
 __global__ void __launch_bounds__(256) k_ghost(Dev<T> D)
 {
-    ghost_body<T, MK_BATCH_ONE>(D, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    ghost_body<T, MB>(D, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 // Ghost layers of Q at t_{n+1} (after the y-line solves), for F*(Q^{n+1}).
@@ -2649,10 +2653,11 @@ __global__ void k_setup_centres(Dev<T> D, SetupArgs A)
 // mirror of the normal flux (the outside coefficient moves onto the diagonal),
 // maker = the outside value is known (its coefficient goes to cW..cN).  The
 // rows of Eq. 21 come from the still depth with reciprocals of the cell size
-// taken once, so the only division of a step is its pivot's: the pivots form
-// a chain along the line, and with a few hundred lines on the device each
-// thread's chain of double-precision divisions is what the set-up waits on.
-// One warp per block spreads the lines over the multiprocessors.
+// taken once, so the only division of a step is its pivot's.  The still depth
+// ahead is loaded 16 cells at a time: a thread walks its whole line, and a
+// load waited for at every step (a new row at every step of a column) made
+// the walk a chain of memory latencies.  One warp per block spreads the lines
+// over the multiprocessors.
 template <typename T>
 __global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
 {
@@ -2671,22 +2676,31 @@ __global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
     auto at = [&](int k) { return xline ? fidx(D, k, line) : fidx(D, line, k); };
     double dm = A.dd[at(-1)], d0 = A.dd[at(0)];
     double cprev = 0.0;
-    for (int k = 0; k < n; k++) {
-        const double dp = A.dd[at(k + 1)];
-        const double gd = (dp - dm) * r2h;
-        const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
-        double a = t1 - t2, b = 1.0 + 2.0 * t2, c = -t1 - t2;
-        if (k == 0) { cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
-        if (k == n - 1) { clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
-        if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
-        const double m = 1.0 / (b - a * cprev);
-        cprev = c * m;
-        const long long o = at(k);
-        fm[o] = (T)m;
-        fe[o] = (T)(-a * m);
-        fc[o] = (T)cprev;
-        dm = d0;
-        d0 = dp;
+    constexpr int CH = 16;
+    for (int k0 = 0; k0 < n; k0 += CH) {
+        double dn[CH];  // still depth at cells k0 + 1 .. k0 + CH (cell n is the ghost cell)
+#pragma unroll
+        for (int q = 0; q < CH; q++) dn[q] = k0 + q + 1 <= n ? A.dd[at(k0 + q + 1)] : 0.0;
+#pragma unroll
+        for (int q = 0; q < CH; q++) {
+            const int k = k0 + q;
+            if (k >= n) break;
+            const double dp = dn[q];
+            const double gd = (dp - dm) * r2h;
+            const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
+            double a = t1 - t2, b = 1.0 + 2.0 * t2, c = -t1 - t2;
+            if (k == 0) { cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
+            if (k == n - 1) { clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
+            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+            const double m = 1.0 / (b - a * cprev);
+            cprev = c * m;
+            const long long o = at(k);
+            fm[o] = (T)m;
+            fe[o] = (T)(-a * m);
+            fc[o] = (T)cprev;
+            dm = d0;
+            d0 = dp;
+        }
     }
 }
 
@@ -3054,7 +3068,8 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     long long nwork = 4LL * ny + 4LL * (nx + 4) + 2LL * ny + 2LL * nx;
     int gb = (int)((nwork + 255) / 256);
     if (ev) cudaEventRecord(ev[0], st);
-    k_ghost<T><<<gb, 256, ghost_smem(D), st>>>(D);
+    if (D.ncomp <= MK_FEW) k_ghost<T, MK_FEW><<<gb, 256, ghost_smem(D), st>>>(D);
+    else k_ghost<T><<<gb, 256, ghost_smem(D), st>>>(D);
     if (ev) cudaEventRecord(ev[1], st);
     const int rows = rhs_rows(D);
     const int nstrip = (nx + SW_COLS - 1) / SW_COLS;
