@@ -93,9 +93,10 @@ static bsq_status set_sticky(bsq_domain *d, bsq_status s)
     return s;
 }
 
-// Bounded wait for a stream: polls cudaStreamQuery, yielding for the first
-// 2 ms and then sleeping a fiftieth of the time waited so far (at most 1 ms),
-// so completion is seen within about 2 % of the wait.
+// Bounded wait for a stream: polls cudaStreamQuery, yielding the thread
+// between polls for the first 20 ms (a sleep overshoots by tens of
+// microseconds, a few percent of a call of a few milliseconds) and sleeping
+// 50 us between polls after that.
 static bsq_status bounded_wait(cudaStream_t st, double lim)
 {
     auto t0 = std::chrono::steady_clock::now();
@@ -105,8 +106,8 @@ static bsq_status bounded_wait(cudaStream_t st, double lim)
         if (e != cudaErrorNotReady) return BSQ_ERR_CUDA;
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > lim) return BSQ_ERR_TIMEOUT;
-        if (el < 2e-3) std::this_thread::yield();
-        else std::this_thread::sleep_for(std::chrono::microseconds((long long)fmin(1000.0, el * 0.02 * 1e6)));
+        if (el < 20e-3) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
 }
 
