@@ -2653,34 +2653,42 @@ __global__ void k_setup_centres(Dev<T> D, SetupArgs A)
 // mirror of the normal flux (the outside coefficient moves onto the diagonal),
 // maker = the outside value is known (its coefficient goes to cW..cN).  The
 // rows of Eq. 21 come from the still depth with reciprocals of the cell size
-// taken once, so the only division of a step is its pivot's.  The still depth
-// ahead is loaded 16 cells at a time: a thread walks its whole line, and a
-// load waited for at every step (a new row at every step of a column) made
-// the walk a chain of memory latencies.  One warp per block spreads the lines
-// over the multiprocessors.
+// taken once, so the only division of a step is its pivot's.  A thread walks
+// its whole line 16 cells at a time: it loads the still depth of the 16 cells
+// ahead at once (a load waited for at every step, a new row at every step of
+// a column, made the walk a chain of memory latencies), and an x-line warp
+// writes its 32 rows' 16 results through shared memory, a row's 16 values at
+// a time (a thread per row writing alone scatters every store over 32 rows).
+// One warp per block: blocks 0 .. ceil(ny/32)-1 take x-lines, the rest
+// y-lines, so a block's lines all run the same way.
 template <typename T>
 __global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int CH = 16;
+    __shared__ T tile[3][CH][33];
+    const int lane = threadIdx.x;
     const double kB = A.Bd + 1.0 / 3.0;
     const int nx = D.nx, ny = D.ny;
-    const bool xline = t < ny;
-    if (!xline && t >= ny + nx) return;
+    const int nbx = (ny + 31) / 32;
+    const bool xline = (int)blockIdx.x < nbx;
+    const int line0 = (xline ? (int)blockIdx.x : (int)blockIdx.x - nbx) * 32;
+    const int line = line0 + lane;
+    const int nlines = xline ? ny : nx;
+    if (line0 >= nlines) return;  // (block-uniform)
+    const bool valid = line < nlines;
     const int n = xline ? nx : ny;
     const double h = xline ? A.dx : A.dy;
     const double r2h = 0.5 / h, r6h = 1.0 / (6.0 * h), rh2 = 1.0 / (h * h);
     const int lo = xline ? A.bt[0] : A.bt[2], hi = xline ? A.bt[1] : A.bt[3];
     double *cfirst = xline ? A.cW : A.cS, *clast = xline ? A.cE : A.cN;
     T *fm = xline ? D.fxm : D.fym, *fe = xline ? D.fxe : D.fye, *fc = xline ? D.fxc : D.fyc;
-    const int line = xline ? t : t - ny;
-    auto at = [&](int k) { return xline ? fidx(D, k, line) : fidx(D, line, k); };
-    double dm = A.dd[at(-1)], d0 = A.dd[at(0)];
+    auto at = [&](int k, int l) { return xline ? fidx(D, k, l) : fidx(D, l, k); };
+    double dm = valid ? A.dd[at(-1, line)] : 1.0, d0 = valid ? A.dd[at(0, line)] : 1.0;
     double cprev = 0.0;
-    constexpr int CH = 16;
     for (int k0 = 0; k0 < n; k0 += CH) {
         double dn[CH];  // still depth at cells k0 + 1 .. k0 + CH (cell n is the ghost cell)
 #pragma unroll
-        for (int q = 0; q < CH; q++) dn[q] = k0 + q + 1 <= n ? A.dd[at(k0 + q + 1)] : 0.0;
+        for (int q = 0; q < CH; q++) dn[q] = valid && k0 + q + 1 <= n ? A.dd[at(k0 + q + 1, line)] : 1.0;
 #pragma unroll
         for (int q = 0; q < CH; q++) {
             const int k = k0 + q;
@@ -2689,17 +2697,37 @@ __global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
             const double gd = (dp - dm) * r2h;
             const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
             double a = t1 - t2, b = 1.0 + 2.0 * t2, c = -t1 - t2;
-            if (k == 0) { cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
-            if (k == n - 1) { clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
-            if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+            if (k == 0) { if (valid) cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
+            if (k == n - 1) { if (valid) clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
+            if (valid && !(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
             const double m = 1.0 / (b - a * cprev);
             cprev = c * m;
-            const long long o = at(k);
-            fm[o] = (T)m;
-            fe[o] = (T)(-a * m);
-            fc[o] = (T)cprev;
+            if (xline) {
+                tile[0][q][lane] = (T)m;
+                tile[1][q][lane] = (T)(-a * m);
+                tile[2][q][lane] = (T)cprev;
+            } else if (valid) {
+                const long long o = at(k, line);
+                fm[o] = (T)m;
+                fe[o] = (T)(-a * m);
+                fc[o] = (T)cprev;
+            }
             dm = d0;
             d0 = dp;
+        }
+        if (xline) {
+            // the warp writes the chunk of its 32 rows: two rows of 16 values a pass
+            __syncwarp();
+            for (int idx = lane; idx < 32 * CH; idx += 32) {
+                const int rr = idx / CH, q = idx - rr * CH, k = k0 + q;
+                if (k < n && line0 + rr < ny) {
+                    const long long o = at(k, line0 + rr);
+                    fm[o] = tile[0][q][rr];
+                    fe[o] = tile[1][q][rr];
+                    fc[o] = tile[2][q][rr];
+                }
+            }
+            __syncwarp();
         }
     }
 }
@@ -2737,7 +2765,7 @@ cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
     k_setup_fill<T><<<gs, 256, 0, st>>>(D);
     k_setup_corner<T><<<gs, 256, 0, st>>>(D, A);
     k_setup_centres<T><<<gs, 256, 0, st>>>(D, A);
-    k_setup_factors<T><<<(D.nx + D.ny + 31) / 32, 32, 0, st>>>(D, A);
+    k_setup_factors<T><<<(D.ny + 31) / 32 + (D.nx + 31) / 32, 32, 0, st>>>(D, A);
     k_setup_state<T><<<gs, 256, 0, st>>>(D, A);
     return cudaGetLastError();
 }
