@@ -192,8 +192,13 @@ def bsq_step_dt(h, dts) -> None:
         raise BsqError(st, "bsq_step_dt")
 
 
-def bsq_read(h, field: int, nx: int, ny: int) -> np.ndarray:
-    out = np.empty((ny, nx), dtype=np.float64)
+def bsq_read(h, field: int, nx: int, ny: int, out=None) -> np.ndarray:
+    """Field into ``out`` ((ny, nx) float64, C-contiguous; e.g. a view of
+    page-locked memory) or a new array."""
+    if out is None:
+        out = np.empty((ny, nx), dtype=np.float64)
+    elif out.shape != (ny, nx) or out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous (ny, nx) float64 array")
     st = lib().bsq_read(h, int(field), _ptr(out))
     if st != OK:
         raise BsqError(st, "bsq_read")
@@ -371,8 +376,8 @@ class Domain:
     def step_dt(self, dts) -> None:
         bsq_step_dt(self.h, dts)
 
-    def read(self, field: str) -> np.ndarray:
-        return bsq_read(self.h, FIELDS[field], self.nx, self.ny)
+    def read(self, field: str, out=None) -> np.ndarray:
+        return bsq_read(self.h, FIELDS[field], self.nx, self.ny, out)
 
     def read_device(self, field: str, dev_ptr: int) -> None:
         bsq_read_device(self.h, FIELDS[field], dev_ptr)

@@ -387,3 +387,21 @@ def test_advance_to_t_end_after_restore_and_batch():
         assert b.advance(t_end=t_end) >= 1
         assert abs(b.info()["t"] - t_end) <= 1e-12 * max(1.0, t_end)
         assert b.advance(max_steps=3) == 3 and b.info()["n"] > 15
+
+
+def test_read_into_caller_array():
+    # bsq_read into a caller-owned array (here page-locked memory, as the end-to-end
+    # benchmark passes it) gives the same values as into a new array; a wrong
+    # shape or type is refused before any device work
+    import torch
+
+    case = W.barred_beach(nx=96, ny=72)
+    with bsq.Domain(case, precision="fp32") as d:
+        d.advance(max_steps=12)
+        out = torch.empty((72, 96), dtype=torch.float64, pin_memory=True).numpy()
+        for f in ("eta", "P", "Q", "h", "w"):
+            np.testing.assert_array_equal(d.read(f, out=out), d.read(f))
+        with pytest.raises(ValueError):
+            d.read("eta", out=np.empty((96, 72)))
+        with pytest.raises(ValueError):
+            d.read("eta", out=np.empty((72, 96), dtype=np.float32))
