@@ -2648,25 +2648,47 @@ __global__ void k_setup_centres(Dev<T> D, SetupArgs A)
     }
 }
 
-// Thomas factors (m, -a m, c' = c m) of every x-line (one thread per row) and
-// y-line (one thread per column), boundary rows closed: wall or sponge = odd
-// mirror of the normal flux (the outside coefficient moves onto the diagonal),
-// maker = the outside value is known (its coefficient goes to cW..cN).  The
-// rows of Eq. 21 come from the still depth with reciprocals of the cell size
-// taken once, so the only division of a step is its pivot's.  A thread walks
-// its whole line 16 cells at a time: it loads the still depth of the 16 cells
-// ahead at once (a load waited for at every step, a new row at every step of
-// a column, made the walk a chain of memory latencies), and an x-line warp
-// writes its 32 rows' 16 results through shared memory, a row's 16 values at
-// a time (a thread per row writing alone scatters every store over 32 rows).
-// One warp per block: blocks 0 .. ceil(ny/32)-1 take x-lines, the rest
-// y-lines, so a block's lines all run the same way.
+// Thomas factors (m, -a m, c' = c m) of every x-line and y-line, boundary
+// rows closed: wall or sponge = odd mirror of the normal flux (the outside
+// coefficient moves onto the diagonal), maker = the outside value is known
+// (its coefficient goes to cW..cN).  The rows of Eq. 21 come from the still
+// depth with reciprocals of the cell size taken once.
+//
+// The pivots p_k = b_k - a_k c_{k-1} / p_{k-1} (m_k = 1 / p_k) are ratios
+// p_k = u_k / u_{k-1} of the linear recurrence u_k = b_k u_{k-1} - a_k c_{k-1}
+// u_{k-2} (u_{-1} = 1, u_{-2} = 0), whose step is the 2x2 matrix
+// [[b_k, -a_k c_{k-1}], [1, 0]] acting on (u_{k-1}, u_{k-2}).  A line is cut
+// into FS_SEG segments, one thread each: every thread multiplies its
+// segment's matrices, the product of the segments before it gives the state
+// its segment starts from, and a second walk of the segment produces the
+// factors.  The recurrence carries its dominant solution, so the segments'
+// rounding does not grow (about 1e-14 relative against 1e-15 for one walk
+// along the line); states and products are rescaled by exact powers of two.
+// A block holds 32 lines (lanes) x FS_SEG segments (warps), x-lines in blocks
+// 0 .. ceil(ny/32)-1 and y-lines after them; the still depth is loaded FS_CH
+// cells ahead, and an x-line warp writes its rows through shared memory,
+// FS_CH consecutive values of a row at a time.
+constexpr int FS_SEG = 8, FS_CH = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
+static size_t setup_factors_smem()
 {
-    constexpr int CH = 16;
-    __shared__ T tile[3][CH][33];
-    const int lane = threadIdx.x;
+    return (size_t)FS_SEG * 32 * 4 * sizeof(double) + (size_t)FS_SEG * 3 * FS_CH * 33 * sizeof(T);
+}
+
+__device__ __forceinline__ double pow2_inv_scale(double x)
+{
+    return x == 0.0 ? 1.0 : scalbn(1.0, -ilogb(x));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * FS_SEG) k_setup_factors(Dev<T> D, SetupArgs A)
+{
+    extern __shared__ __align__(16) unsigned char fs_smem[];
+    double *Gs = reinterpret_cast<double *>(fs_smem);  // [FS_SEG][32][4]
+    T *tile = reinterpret_cast<T *>(fs_smem + (size_t)FS_SEG * 32 * 4 * sizeof(double)) +
+              (size_t)(threadIdx.x >> 5) * 3 * FS_CH * 33;  // this warp's [3][FS_CH][33]
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const double kB = A.Bd + 1.0 / 3.0;
     const int nx = D.nx, ny = D.ny;
     const int nbx = (ny + 31) / 32;
@@ -2677,54 +2699,122 @@ __global__ void __launch_bounds__(32) k_setup_factors(Dev<T> D, SetupArgs A)
     if (line0 >= nlines) return;  // (block-uniform)
     const bool valid = line < nlines;
     const int n = xline ? nx : ny;
+    const int S = (n + FS_SEG - 1) / FS_SEG;
+    const int kb = min(n, seg * S), ke = min(n, kb + S);
     const double h = xline ? A.dx : A.dy;
     const double r2h = 0.5 / h, r6h = 1.0 / (6.0 * h), rh2 = 1.0 / (h * h);
     const int lo = xline ? A.bt[0] : A.bt[2], hi = xline ? A.bt[1] : A.bt[3];
     double *cfirst = xline ? A.cW : A.cS, *clast = xline ? A.cE : A.cN;
     T *fm = xline ? D.fxm : D.fym, *fe = xline ? D.fxe : D.fye, *fc = xline ? D.fxc : D.fyc;
     auto at = [&](int k, int l) { return xline ? fidx(D, k, l) : fidx(D, l, k); };
-    double dm = valid ? A.dd[at(-1, line)] : 1.0, d0 = valid ? A.dd[at(0, line)] : 1.0;
-    double cprev = 0.0;
-    for (int k0 = 0; k0 < n; k0 += CH) {
-        double dn[CH];  // still depth at cells k0 + 1 .. k0 + CH (cell n is the ghost cell)
+    auto dd = [&](int k) { return valid ? A.dd[at(k, line)] : 1.0; };
+    // row k of the line from the still depth at k-1, k, k+1, ends closed;
+    // `outside` receives the coefficient of the outside neighbour at an end
+    auto row = [&](int k, double dm, double d0, double dp, double &a, double &b, double &c, double &outside) {
+        const double gd = (dp - dm) * r2h;
+        const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
+        a = t1 - t2;
+        b = 1.0 + 2.0 * t2;
+        c = -t1 - t2;
+        if (k == 0) { outside = a; if (lo != MAKER) b -= a; a = 0.0; }
+        if (k == n - 1) { outside = c; if (hi != MAKER) b -= c; c = 0.0; }
+    };
+    // c of the row before the segment (a_kb multiplies it)
+    double cprev0 = 0.0;
+    if (kb > 0 && kb < n) {
+        double a, b, c, o;
+        row(kb - 1, dd(kb - 2), dd(kb - 1), dd(kb), a, b, c, o);
+        cprev0 = c;
+    }
+
+    // ---- pass 1: product of the segment's step matrices
+    double g00 = 1.0, g01 = 0.0, g10 = 0.0, g11 = 1.0;
+    {
+        double dm = kb < n ? dd(kb - 1) : 1.0, d0 = kb < n ? dd(kb) : 1.0, cprev = cprev0;
+        for (int k0 = kb; k0 < ke; k0 += FS_CH) {
+            double dn[FS_CH];
 #pragma unroll
-        for (int q = 0; q < CH; q++) dn[q] = valid && k0 + q + 1 <= n ? A.dd[at(k0 + q + 1, line)] : 1.0;
+            for (int q = 0; q < FS_CH; q++) dn[q] = k0 + q < ke ? dd(k0 + q + 1) : 1.0;
 #pragma unroll
-        for (int q = 0; q < CH; q++) {
+            for (int q = 0; q < FS_CH; q++) {
+                const int k = k0 + q;
+                if (k >= ke) break;
+                double a, b, c, o;
+                row(k, dm, d0, dn[q], a, b, c, o);
+                const double qa = a * cprev;
+                const double n00 = b * g00 - qa * g10, n01 = b * g01 - qa * g11;
+                g10 = g00;
+                g11 = g01;
+                g00 = n00;
+                g01 = n01;
+                cprev = c;
+                dm = d0;
+                d0 = dn[q];
+            }
+            const double sc = pow2_inv_scale(fmax(fmax(fabs(g00), fabs(g01)), fmax(fabs(g10), fabs(g11))));
+            g00 *= sc; g01 *= sc; g10 *= sc; g11 *= sc;
+        }
+    }
+    double *gme = Gs + ((size_t)seg * 32 + lane) * 4;
+    gme[0] = g00; gme[1] = g01; gme[2] = g10; gme[3] = g11;
+    __syncthreads();
+    // state (u_{kb-1}, u_{kb-2}) from the products of the segments before
+    double u = 1.0, v = 0.0;
+    for (int s2 = 0; s2 < seg; s2++) {
+        const double *gp = Gs + ((size_t)s2 * 32 + lane) * 4;
+        const double nu = gp[0] * u + gp[1] * v, nv = gp[2] * u + gp[3] * v;
+        const double sc = pow2_inv_scale(fmax(fabs(nu), fabs(nv)));
+        u = nu * sc;
+        v = nv * sc;
+    }
+
+    // ---- pass 2: the factors
+    double dm = kb < n ? dd(kb - 1) : 1.0, d0 = kb < n ? dd(kb) : 1.0, cprev = cprev0;
+    for (int k0 = kb; k0 < ke; k0 += FS_CH) {
+        double dn[FS_CH];
+#pragma unroll
+        for (int q = 0; q < FS_CH; q++) dn[q] = k0 + q < ke ? dd(k0 + q + 1) : 1.0;
+#pragma unroll
+        for (int q = 0; q < FS_CH; q++) {
             const int k = k0 + q;
-            if (k >= n) break;
-            const double dp = dn[q];
-            const double gd = (dp - dm) * r2h;
-            const double t1 = d0 * gd * r6h, t2 = kB * d0 * d0 * rh2;
-            double a = t1 - t2, b = 1.0 + 2.0 * t2, c = -t1 - t2;
-            if (k == 0) { if (valid) cfirst[line] = a; if (lo != MAKER) b -= a; a = 0.0; }
-            if (k == n - 1) { if (valid) clast[line] = c; if (hi != MAKER) b -= c; c = 0.0; }
-            if (valid && !(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
-            const double m = 1.0 / (b - a * cprev);
-            cprev = c * m;
+            if (k >= ke) break;
+            double a, b, c, o = 0.0;
+            row(k, dm, d0, dn[q], a, b, c, o);
+            if (valid) {
+                if (k == 0) cfirst[line] = o;
+                if (k == n - 1) clast[line] = o;
+                if (!(fabs(b) > fabs(a) + fabs(c))) atomicOr(A.bad, 1u);
+            }
+            const double un = fma(b, u, -(a * cprev) * v);  // u_k
+            const double m = u / un;                          // 1 / p_k
+            v = u;
+            u = un;
+            cprev = c;
+            dm = d0;
+            d0 = dn[q];
             if (xline) {
-                tile[0][q][lane] = (T)m;
-                tile[1][q][lane] = (T)(-a * m);
-                tile[2][q][lane] = (T)cprev;
+                tile[(0 * FS_CH + q) * 33 + lane] = (T)m;
+                tile[(1 * FS_CH + q) * 33 + lane] = (T)(-a * m);
+                tile[(2 * FS_CH + q) * 33 + lane] = (T)(c * m);
             } else if (valid) {
                 const long long o = at(k, line);
                 fm[o] = (T)m;
                 fe[o] = (T)(-a * m);
-                fc[o] = (T)cprev;
+                fc[o] = (T)(c * m);
             }
-            dm = d0;
-            d0 = dp;
         }
+        const double sc = pow2_inv_scale(u);
+        u *= sc;
+        v *= sc;
         if (xline) {
-            // the warp writes the chunk of its 32 rows: two rows of 16 values a pass
             __syncwarp();
-            for (int idx = lane; idx < 32 * CH; idx += 32) {
-                const int rr = idx / CH, q = idx - rr * CH, k = k0 + q;
-                if (k < n && line0 + rr < ny) {
+            for (int idx = lane; idx < 32 * FS_CH; idx += 32) {
+                const int rr = idx / FS_CH, q = idx - rr * FS_CH, k = k0 + q;
+                if (k < ke && line0 + rr < ny) {
                     const long long o = at(k, line0 + rr);
-                    fm[o] = tile[0][q][rr];
-                    fe[o] = tile[1][q][rr];
-                    fc[o] = tile[2][q][rr];
+                    fm[o] = tile[(0 * FS_CH + q) * 33 + rr];
+                    fe[o] = tile[(1 * FS_CH + q) * 33 + rr];
+                    fc[o] = tile[(2 * FS_CH + q) * 33 + rr];
                 }
             }
             __syncwarp();
@@ -2765,7 +2855,10 @@ cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
     k_setup_fill<T><<<gs, 256, 0, st>>>(D);
     k_setup_corner<T><<<gs, 256, 0, st>>>(D, A);
     k_setup_centres<T><<<gs, 256, 0, st>>>(D, A);
-    k_setup_factors<T><<<(D.ny + 31) / 32 + (D.nx + 31) / 32, 32, 0, st>>>(D, A);
+    const size_t fsm = setup_factors_smem<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_setup_factors<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    if (e != cudaSuccess) return e;
+    k_setup_factors<T><<<(D.ny + 31) / 32 + (D.nx + 31) / 32, 32 * FS_SEG, fsm, st>>>(D, A);
     k_setup_state<T><<<gs, 256, 0, st>>>(D, A);
     return cudaGetLastError();
 }

@@ -69,6 +69,18 @@ def _maker_case(nx, ny, bc, seed, dx=0.1):
     return dict(params=prm, bed=bed, comps=comps, eta0=None, P0=None, Q0=None)
 
 
+def _tall_solitary(nx, ny, dx=0.05, depth=0.6, amp=0.06):
+    # a solitary wave travelling along y in a column taller than one pass of
+    # the y-line chunk scan (more than 256 chunks of 8 rows); the 2D target CFL
+    # of reading R2 (round-off across the column seeds the 2D modes that a
+    # CFL of 0.2 lets grow)
+    yc = (np.arange(ny) + 0.5) * dx
+    eta1, q1 = W.solitary_profile(yc, 0.3 * ny * dx, amp, depth)
+    bed = np.full((ny + 1, nx + 1), -depth)
+    return dict(params=W.base_params(nx, ny, dx, cfl=0.125), bed=bed, comps=None,
+                eta0=np.tile(eta1[:, None], (1, nx)), P0=None, Q0=np.tile(q1[:, None], (1, nx)))
+
+
 CASES = {
     "hump_2d_walls": lambda: _hump_case(77, 45),
     "barred_beach_rips": lambda: W.barred_beach(nx=96, ny=72),
@@ -77,6 +89,7 @@ CASES = {
     "ragged_multi_segment": lambda: _hump_case(301, 37, dx=0.05, seed=5),
     "tall_multi_chunk": lambda: _hump_case(35, 530, dx=0.05, seed=7),
     "tall_multi_segment": lambda: _hump_case(19, 2309, dx=0.05, seed=17),
+    "tall_solitary_multi_segment": lambda: _tall_solitary(12, 2309),
     "random_basin_jonswap": lambda: W.random_basin(64, seed=13, forcing="jonswap"),
     "hamm_rip_friction": lambda: W.hamm_rip(nx=100, ny=60),
     "makers_four_sides_oblique": lambda: _maker_case(70, 58, (W.MAKER,) * 4, seed=21),
@@ -174,7 +187,7 @@ def test_fp64_advance_lands_on_t_end_like_oracle():
 
 @pytest.mark.parametrize("name", ["barred_beach_rips", "hump_2d_walls", "planar_beach_jonswap",
                                   "random_basin_jonswap", "hamm_rip_friction", "makers_four_sides_oblique",
-                                  "makers_west_east_oblique"])
+                                  "makers_west_east_oblique", "tall_solitary_multi_segment"])
 def test_fp32_kahan_1000_steps_matches_oracle(name):
     case = CASES[name]()
     o = _oracle(case)
