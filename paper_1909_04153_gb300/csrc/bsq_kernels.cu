@@ -163,36 +163,6 @@ __device__ __forceinline__ void load_halo_chunk(const T *row, int ib, int lane, 
 // to 8, so a lane's 8 chunks are one aligned vector
 __host__ __device__ __forceinline__ int ychunk_stride(int nch) { return (nch + 7) & ~7; }
 
-// ---- single-precision x-line factors from the still depth
-//
-// The rows of Eq. 21 are local in the still depth d: a = t1 - t2 and
-// c = -t1 - t2 with t1 = d d' / (6 h), d' the central difference of d along
-// the line, and t2 = (B + 1/3) d^2 / h^2.  The Thomas pivots m are a
-// recurrence along the line and stay stored (computed in FP64 at set-up).
-// The single-precision warp-per-row x-solver forms -a m and c m from d and
-// m instead of reading two more stored fields (two fewer values per cell
-// from memory); its forward and backward passes take d from the same bed
-// values and round in the same order, so both use bitwise the same factors.
-// The y-line kernels keep the stored factors: forming them there cost
-// k_yapply occupancy and time.
-struct LineK {
-    float half_r, s6, kr;  // 1/(2h), 1/(6h), (B + 1/3)/h^2
-};
-__device__ __forceinline__ LineK line_k(float r, float Bd)
-{
-    LineK k;
-    k.half_r = 0.5f * r;
-    k.s6 = __fmul_rn(1.0f / 6.0f, r);
-    k.kr = __fmul_rn(__fadd_rn(Bd, 1.0f / 3.0f), __fmul_rn(r, r));
-    return k;
-}
-// t1 and t2 of the row of a cell with still depth d0, neighbours dm, dp
-__device__ __forceinline__ void eq21_t(const LineK &k, float dm, float d0, float dp, float &t1, float &t2)
-{
-    const float dd = __fmul_rn(__fsub_rn(dp, dm), k.half_r);
-    t1 = __fmul_rn(__fmul_rn(d0, dd), k.s6);
-    t2 = __fmul_rn(__fmul_rn(d0, d0), k.kr);
-}
 // KP07 bed at a cell centre from its corners k00 = (i, j), k10 = (i+1, j),
 // k01 = (i, j+1), k11 = (i+1, j+1): the mean of the four face values, each
 // face the mean of its two corners, rounded step by step in this order
@@ -2354,11 +2324,6 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
     const T corrW = D.corrW[j], corrE = D.corrE[j];
     const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
     const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
-    // single precision with the sequential cross form: -a m and c m of Eq. 21
-    // from the still depth (see eq21_t), only the pivots m are read
-    constexpr bool F32 = sizeof(T) == 4;
-    const bool fly = F32 && seq;
-    const LineK lkx = line_k((float)D.rdx, (float)D.Bd);
     T carry = (T)0;
     int c0 = 0;
     for (; c0 < nx; c0 += 32 * K) {
@@ -2369,7 +2334,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
         T r[K], m[K], e[K];
         vload_k_if<T, K>(act, D.dU + rowo + ib, r);
         vload_k_if<T, K>(act, D.fxm + rowo + ib, m);
-        if (!fly) vload_k_if<T, K>(act, D.fxe + rowo + ib, e);
+        vload_k_if<T, K>(act, D.fxe + rowo + ib, e);
         if (seq) {
             T Qc[K + 2], bc_[K + 2], qm[K + 2], qp[K + 2], bm[K], bp[K];
             load_halo_chunk_if<T, K>(act, Qr, ib, lane, Qc);
@@ -2403,15 +2368,6 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
                     const T gv = D.bc[side] == MAKER ? mq[min(max(cc, -1), nx) + 1] : -Qc[q];
                     if (j == 0) qm[q] = gv;
                     else qp[q] = gv;
-                }
-            }
-            if constexpr (F32) {
-#pragma unroll
-                for (int q = 0; q < K; q++) {
-                    float t1, t2;
-                    eq21_t(lkx, tmax(D.w_s - bc_[q], 0.0f), tmax(D.w_s - bc_[q + 1], 0.0f),
-                           tmax(D.w_s - bc_[q + 2], 0.0f), t1, t2);
-                    e[q] = ib + q == 0 ? 0.0f : __fmul_rn(__fsub_rn(t2, t1), m[q]);
                 }
             }
 #pragma unroll
@@ -2461,28 +2417,12 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
         T x[K], c[K], Pv[K], cPv[K], wv[K], Qv[K], bv[K], gxv[K];
         vload_k<T, K>(ys + ib, x);
         vload_k_if<T, K>(act, D.gx + ib, gxv);
-        vload_k_if<T, K>(act, fly ? D.fxm + rowo + ib : D.fxc + rowo + ib, c);
+        vload_k_if<T, K>(act, D.fxc + rowo + ib, c);
         vload_k_if<T, K>(act, Pr + ib, Pv);
         vload_k_if<T, K>(act && kah, cPr + ib, cPv);
         vload_k_if<T, K>(act, wrow + ib, wv);
         vload_k_if<T, K>(act, Qr + ib, Qv);
-        if (fly) {
-            // c m from the pivots just loaded into c and the still depth
-            T bh[K + 2];
-            load_halo_chunk_if<T, K>(act, br, ib, lane, bh);
-#pragma unroll
-            for (int q = 0; q < K; q++) {
-                bv[q] = bh[q + 1];
-                if constexpr (F32) {
-                    float t1, t2;
-                    eq21_t(lkx, tmax(D.w_s - bh[q], 0.0f), tmax(D.w_s - bh[q + 1], 0.0f),
-                           tmax(D.w_s - bh[q + 2], 0.0f), t1, t2);
-                    c[q] = ib + q == nx - 1 ? 0.0f : -__fmul_rn(__fadd_rn(t1, t2), c[q]);
-                }
-            }
-        } else {
-            vload_k_if<T, K>(act, br + ib, bv);
-        }
+        vload_k_if<T, K>(act, br + ib, bv);
 #pragma unroll
         for (int q = 0; q < K; q++)
             if (ib + q >= nx) { c[q] = (T)0; x[q] = (T)0; }

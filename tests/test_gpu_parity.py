@@ -18,6 +18,16 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 FP64_LINF = 1e-9  # largest cell error, relative to the field's largest magnitude
+# a flux field that is zero in exact arithmetic (the transverse flux of a
+# 1D run) stays at round-off: 2e-15 against a largest Q of 0.15 in the
+# x-invariant column case, where a relative norm says nothing.  A flux field
+# below ROUNDOFF_FLUX times the larger flux field's maximum is compared
+# absolutely, against that maximum.
+ROUNDOFF_FLUX = 1e-12
+
+
+def flux_scale(o):
+    return max(float(np.abs(o.get("P")).max()), float(np.abs(o.get("Q")).max()), 1e-300)
 FP32_TOL = 1e-4
 
 
@@ -110,8 +120,8 @@ def test_fp64_replay_matches_oracle(name):
         assert abs(info["t"] - o.info()["t"]) <= 1e-12 * o.info()["t"]
         for f in ("eta", "P", "Q"):
             ref, got = o.get(f), d.read(f)
-            if np.linalg.norm(ref) == 0.0:
-                assert np.abs(got).max() <= 1e-13, f
+            if f != "eta" and np.abs(ref).max() <= ROUNDOFF_FLUX * flux_scale(o):
+                assert np.abs(got).max() <= 1e-11 * flux_scale(o), f
             else:
                 assert rel(got, ref) <= FP64_TOL, (f, rel(got, ref))
                 assert linf(got, ref) <= FP64_LINF, (f, linf(got, ref))
@@ -197,12 +207,12 @@ def test_fp32_kahan_1000_steps_matches_oracle(name):
         e = rel(d.read("eta"), o.get("eta"))
         assert e <= FP32_TOL, e
         # fluxes reported, looser (the oracle itself only pins eta here); a flux
-        # that is exactly zero in the oracle (y-invariant runs: Q) is compared
-        # absolutely
+        # that is zero up to round-off in the oracle (Q of y-invariant runs, P
+        # of x-invariant ones) is compared absolutely
         for f in ("P", "Q"):
             ref = o.get(f)
-            if np.linalg.norm(ref) == 0.0:
-                assert np.abs(d.read(f)).max() <= 1e-6, f
+            if np.abs(ref).max() <= ROUNDOFF_FLUX * flux_scale(o):
+                assert np.abs(d.read(f)).max() <= 1e-5 * flux_scale(o), f
             else:
                 assert rel(d.read(f), ref) <= 1e-3, f
 
