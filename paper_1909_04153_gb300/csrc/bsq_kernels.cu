@@ -38,6 +38,43 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
+// Selections between doubles on the integer pipe.  GB300 runs FP64 at 1/64
+// of the FP32 rate and a compare or a min/max of doubles takes an FP64 issue
+// slot like an add.  The bits of a double read as a signed integer, with the
+// magnitude bits of negative values flipped and -0 taken as +0, order the
+// values exactly as the FP64 compare does (NaNs aside: a non-finite state is
+// flagged anyway), so these pick the same double without the FP64 pipe.
+__device__ __forceinline__ long long dkey(double x)
+{
+    long long i = __double_as_longlong(x);
+    i = i == (long long)0x8000000000000000ULL ? 0LL : i;
+    return i ^ ((i >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double tmax(double a, double b) { return dkey(a) > dkey(b) ? a : b; }
+__device__ __forceinline__ double tmin(double a, double b) { return dkey(a) < dkey(b) ? a : b; }
+template <typename T>
+__device__ __forceinline__ bool tlt(T a, T b) { return a < b; }
+__device__ __forceinline__ bool tlt(double a, double b) { return dkey(a) < dkey(b); }
+template <typename T>
+__device__ __forceinline__ bool tfinite(T x) { return isfinite(x); }
+__device__ __forceinline__ bool tfinite(double x) { return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff; }
+// minmod of two slopes: the one nearer zero when both have the same sign and
+// neither is zero, else 0.  In double precision from the bits: for two
+// positive doubles the smaller integer is the smaller value, for two negative
+// ones the smaller integer is the one nearer zero.
+template <typename T>
+__device__ __forceinline__ T minmod2(T a, T c)
+{
+    const T mn = tmin(a, c), mx = tmax(a, c);
+    return mn > (T)0 ? mn : (mx < (T)0 ? mx : (T)0);
+}
+__device__ __forceinline__ double minmod2(double a, double c)
+{
+    const long long ia = __double_as_longlong(a), ic = __double_as_longlong(c);
+    const bool keep = ((ia ^ ic) >= 0) && ((ia << 1) != 0) && ((ic << 1) != 0);
+    return keep ? __longlong_as_double(ia < ic ? ia : ic) : 0.0;
+}
+
 __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
@@ -60,8 +97,7 @@ __device__ __forceinline__ T gslope(T qm, T q0, T qp, T th)
         // the minmod of the three equals the minmod of a and c (bitwise)
         // (branch-free: both positive -> the smaller, both negative -> the
         // larger, otherwise 0)
-        const T mn = tmin(a, c), mx = tmax(a, c);
-        return mn > (T)0 ? mn : (mx < (T)0 ? mx : (T)0);
+        return minmod2(a, c);
     }
     return minmod3(th * a, (T)0.5 * (qp - qm), th * c);
 }
@@ -98,11 +134,11 @@ __device__ __forceinline__ IvC<double> ivc(double h, double g, double sqrtg, dou
 {
     (void)g;
     const double h2 = h * h, h4 = h2 * h2;
-    const double r = rsqrt(fmax(h, 1e-300));
+    const double r = rsqrt(tmax(h, 1e-300));
     IvC<double> o;
     o.c = sqrtg * h * r;
     o.iv = r * r;
-    if (h4 < eps) o.iv = BSQ_SQRT2 * h * rsqrt(h4 + eps);
+    if (tlt(h4, eps)) o.iv = BSQ_SQRT2 * h * rsqrt(h4 + eps);
     return o;
 }
 
@@ -725,7 +761,7 @@ __device__ __forceinline__ void reconstruct(T wm, T w0, T wp, T Pm, T P0, T Pp, 
     T a = w0 + (T)0.5 * sw, b = w0 - (T)0.5 * sw;
     // positivity: a face value below the face bed is raised to it and the
     // other face value mirrored about w0 (selects, no branches)
-    const bool hi_low = a < bhi, lo_low = !hi_low && b < blo;
+    const bool hi_low = tlt(a, bhi), lo_low = !hi_low && tlt(b, blo);
     wh = hi_low ? bhi : (lo_low ? (T)2 * w0 - blo : a);
     wl = hi_low ? (T)2 * w0 - bhi : (lo_low ? blo : b);
     Pl = P0 - (T)0.5 * sP; Ph = P0 + (T)0.5 * sP;
@@ -764,7 +800,7 @@ __device__ __forceinline__ void cu_flux_st(const FaceSt<T> &L, const FaceSt<T> &
     T ap = tmax(tmax(unL + L.c, unR + R.c), (T)0);
     T am = tmin(tmin(unL - L.c, unR - R.c), (T)0);
     T den = ap - am;
-    const bool moving = den > (T)0;  // a+ = a- = 0: no flux
+    const bool moving = tlt((T)0, den);  // a+ = a- = 0: no flux
     T inv = trcp(moving ? den : (T)1);
     T pL = L.h * L.u, qL = L.h * L.v, pR = R.h * R.u, qR = R.h * R.v;
     T FL0, FL1, FL2, FR0, FR1, FR2;
@@ -846,12 +882,17 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     const int rend = min(j0 + ROWS, ny) + 2;
     // software pipeline: the leading row and the history of the next output
     // row are loaded one step ahead, so their latency overlaps the arithmetic
-    T pw, pP, pQ, pK, pKR;
+    // double precision also loads the bed at the centre, which set-up formed
+    // from the same corners in the same order (bitwise what bed_centre gives
+    // here), instead of twelve FP64 operations a cell
+    constexpr bool BC_LOAD = sizeof(T) == 8;
+    T pw, pP, pQ, pK, pKR, pB = (T)0;
     auto load_lead = [&](int r) {
         const int rr = min(r, ny + 1);
         const long long cr = fidx(D, ic, rr);
         const int kr = min(r + 1, ny + 2);
         pw = w[cr]; pP = D.P[cr]; pQ = D.Q[cr];
+        if (BC_LOAD) pB = D.bC[cr];
         pK = corner[(long long)(kr + 2) * cp + (kc + 2)];
         pKR = corner[(long long)(kr + 2) * cp + (kc1 + 2)];
     };
@@ -893,7 +934,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     load_lead(j0 - 2);
     for (int r = j0 - 2; r < rend; r++) {
         // ---- leading row r (prefetched), bed corners at row r+1
-        T wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR;
+        T wn = pw, Pn = pP, Qn = pQ, Kn = pK, KRn = pKR, Bn = pB;
         T cE1 = hE1, cF1 = hF1, cG1 = hG1, cGs1 = hGs1, cFs1 = hFs1;
         T cE2 = hE2, cF2 = hF2, cG2 = hG2, cGs2 = hGs2, cFs2 = hFs2, ccw = hcw;
         const T cym = hym, cye = hye, cyc = hyc;
@@ -907,7 +948,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
         wW[3] = wn; PW[3] = Pn; QW[3] = Qn; KW[3] = Kn; KRW[3] = KRn;
         // cell-centre bed of row r (mean of its 4 face values), d, eta
         {
-            const T bc = bed_centre(KW[2], KRW[2], KW[3], KRW[3]);
+            const T bc = BC_LOAD ? Bn : bed_centre(KW[2], KRW[2], KW[3], KRW[3]);
             T d = tmax(D.w_s - bc, (T)0);
             bW[2] = bc;
             dW[3] = d;
@@ -1013,7 +1054,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                     const T y = kahan ? dw - ccw : dw;
                     T wnew = w0 + y;
                     T cwn = kahan ? (wnew - w0) - y : (T)0;
-                    const bool cl = wnew < bc;
+                    const bool cl = tlt(wnew, bc);
                     wnew = cl ? bc : wnew;
                     cwn = cl ? (T)0 : cwn;
                     nclamp += (valid && cl) ? 1ull : 0ull;
@@ -1063,7 +1104,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 } else {
                     wnew = w0 + dw;
                 }
-                if (wnew < bc) { wnew = bc; cwn = (T)0; nclamp++; }
+                if (tlt(wnew, bc)) { wnew = bc; cwn = (T)0; nclamp++; }
                 D.w[cf.wc ^ 1][c] = wnew;
                 if (kahan) D.cw[c] = cwn;
                 D.dU[c] = dU;
@@ -1749,7 +1790,7 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
         }
         const int j = j0 + q;
         T gm = gxi * D.gy[min(j, ny - 1)];
-        if (gm < (T)1) { Qn *= gm; cn *= gm; }
+        if (tlt(gm, (T)1)) { Qn *= gm; cn *= gm; }
         Qo[q] = Qn;
         cq[q] = cn;
     }
@@ -1953,7 +1994,7 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         }
         T wq = wv[q];
         T gm = D.gx[i] * gyj;
-        if (gm < (T)1) {
+        if (tlt(gm, (T)1)) {
             T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
             wq = bv[q] + (d + gm * (h - d));
             wr[i] = wq;
@@ -1968,7 +2009,7 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         T u = ic.iv * Pn, v = ic.iv * Qv[q];
         T cc = ic.c;
         rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
-        if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+        if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
     }
     vstore_k<T, K>(Pr + ib, Pv);
     if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
@@ -2247,7 +2288,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             }
             T wq = wv[q];
             T gm = D.gx[i] * gyj;
-            if (gm < (T)1) {
+            if (tlt(gm, (T)1)) {
                 T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
                 wq = bv[q] + (d + gm * (h - d));
                 wrow[i] = wq;
@@ -2262,7 +2303,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
-            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+            if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
         }
         if (ib < nx) {
             vstore_k<T, K>(Pr + ib, Pv);
@@ -2455,7 +2496,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             }
             T wq = wv[q];
             T gm = gxv[q] * gyj;
-            if (gm < (T)1) {
+            if (tlt(gm, (T)1)) {
                 T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
                 wq = bv[q] + (d + gm * (h - d));
                 wrow[i] = wq;
@@ -2470,7 +2511,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
-            if (!isfinite(wq) || !isfinite(Pn) || !isfinite(Qv[q])) bad = true;
+            if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
         }
         if (ib < nx) {
             vstore_k<T, K>(Pr + ib, Pv);
