@@ -195,6 +195,33 @@ extern "C" size_t bsq_domain_bytes(const bsq_params *p, int n_comp)
     return layout<float>(p->nx, p->ny, p->tune[4], p->kahan != 0, n_comp).total;
 }
 
+
+// The smallest double H with (H H)(H H) >= eps, each product rounded to
+// double.  Rounding keeps order, so the rounded h^4 grows with h and, for
+// h >= 0, h < H exactly when the rounded (h h)(h h) < eps: the near-dry test
+// of the double-precision kernels compares h with H and forms h^4 only below
+// it.  Bisection over the bit patterns of the non-negative doubles, which are
+// ordered like the values.
+static double dry_threshold(double eps)
+{
+    auto h4_reaches = [eps](uint64_t bits) {
+        double h;
+        memcpy(&h, &bits, sizeof h);
+        volatile double h2 = h * h;
+        volatile double h4 = h2 * h2;
+        return h4 >= eps;
+    };
+    uint64_t lo = 0, hi = 0x7ff0000000000000ULL;  // +0 .. +inf, and inf^4 >= eps
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (h4_reaches(mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    double H;
+    memcpy(&H, &lo, sizeof H);
+    return H;
+}
+
 template <typename T>
 static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0, const double *P0,
                            const double *Q0)
@@ -302,9 +329,11 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.g = (T)p.g; D.Bd = (T)p.Bd; D.w_s = (T)p.w_s; D.friction = (T)p.friction; D.theta = (T)p.theta;
     double eps = p.eps > 0.0 ? p.eps : pow(fmax(p.dx, p.dy), 4);
     D.eps = (T)eps;
+    D.hdry = sizeof(T) == 8 ? (T)dry_threshold(eps) : (T)0;
     D.kahan = kahan ? 1 : 0;
     D.cross_mode = p.cross_mode;
-    D.tune_rows = p.tune[3] == 16 || p.tune[3] == 24 || p.tune[3] == 32 || p.tune[3] == 48 || p.tune[3] == 64
+    D.tune_rows = p.tune[3] == 16 || p.tune[3] == 24 || p.tune[3] == 32 || p.tune[3] == 48 || p.tune[3] == 64 ||
+                          p.tune[3] == 128
                       ? p.tune[3]
                       : 0;
     D.tune_ysum = (p.tune[6] & 1) ? 1 : 0;

@@ -52,6 +52,7 @@ struct Dev {
     T dx, dy, rdx, rdy;       // cell sizes and reciprocals
     double dxd, dyd;          // cell sizes in FP64 (wave-maker phases)
     T g, Bd, eps, w_s, friction, theta;
+    T hdry;                   // FP64: h < hdry exactly when (h h)(h h) < eps (the near-dry test of KP07)
     int kahan, cross_mode;
     int tune_rows;                 // RHS rows per warp (0: by grid size)
     int tune_xtma;                 // x-solver: 0 automatic, 1 registers only, 3 persistent, 4 warp per row

@@ -120,25 +120,31 @@ __device__ __forceinline__ T desing_inv(T h, T eps)
 // precision, whose square roots and divisions are long instruction sequences
 // at GB300's FP64 rate, takes both from one reciprocal square root r of h
 // where h^4 >= eps: there iv = 1/h exactly, so iv = r^2 and c = sqrt(g) h r;
-// the near-dry side (h^4 < eps) keeps the formula.
+// the near-dry side (h^4 < eps) keeps the formula.  The rounded h^4 grows
+// with h, so h^4 < eps holds exactly below one double, hdry (found once on
+// the host); the test compares h with it, and h^4 is formed only near dry.
 template <typename T>
 struct IvC {
     T iv, c;
 };
-__device__ __forceinline__ IvC<float> ivc(float h, float g, float sqrtg, float eps)
+__device__ __forceinline__ IvC<float> ivc(float h, float g, float sqrtg, float eps, float hdry)
 {
     (void)sqrtg;
+    (void)hdry;
     return {(float)BSQ_SQRT2 * h * desing_inv(h, eps), sqrtf(g * h)};
 }
-__device__ __forceinline__ IvC<double> ivc(double h, double g, double sqrtg, double eps)
+__device__ __forceinline__ IvC<double> ivc(double h, double g, double sqrtg, double eps, double hdry)
 {
     (void)g;
-    const double h2 = h * h, h4 = h2 * h2;
     const double r = rsqrt(tmax(h, 1e-300));
     IvC<double> o;
     o.c = sqrtg * h * r;
     o.iv = r * r;
-    if (tlt(h4, eps)) o.iv = BSQ_SQRT2 * h * rsqrt(h4 + eps);
+    // h >= +0 (or NaN, which fails the test as it fails h^4 < eps)
+    if (__double_as_longlong(h) < __double_as_longlong(hdry)) {
+        const double h2 = h * h, h4 = h2 * h2;
+        o.iv = BSQ_SQRT2 * h * rsqrt(h4 + eps);
+    }
     return o;
 }
 
@@ -751,13 +757,29 @@ __global__ void __launch_bounds__(256) k_ghost_q(Dev<T> D)
 // ------------------------------------------------------------------ RHS + combine
 
 template <typename T>
+__device__ __forceinline__ void reconstruct_tail(T w0, T sw, T P0, T sP, T Q0, T sQ, T blo, T bhi,
+                                                 T &wl, T &wh, T &Pl, T &Ph, T &Ql, T &Qh);
+template <typename T>
 __device__ __forceinline__ void reconstruct(T wm, T w0, T wp, T Pm, T P0, T Pp, T Qm, T Q0, T Qp,
                                             T blo, T bhi, T th, T &wl, T &wh, T &Pl, T &Ph,
                                             T &Ql, T &Qh)
 {
-    T sw = gslope(wm, w0, wp, th);
-    T sP = gslope(Pm, P0, Pp, th);
-    T sQ = gslope(Qm, Q0, Qp, th);
+    reconstruct_tail(w0, gslope(wm, w0, wp, th), P0, gslope(Pm, P0, Pp, th), Q0, gslope(Qm, Q0, Qp, th),
+                     blo, bhi, wl, wh, Pl, Ph, Ql, Qh);
+}
+// theta = 1 from the one-sided differences a = q0 - qm and c = qp - q0, which
+// a caller that walks the cells can pass on from one cell to the next
+template <typename T>
+__device__ __forceinline__ void reconstruct_d(T w0, T aw, T cw, T P0, T aP, T cP, T Q0, T aQ, T cQ,
+                                              T blo, T bhi, T &wl, T &wh, T &Pl, T &Ph, T &Ql, T &Qh)
+{
+    reconstruct_tail(w0, minmod2(aw, cw), P0, minmod2(aP, cP), Q0, minmod2(aQ, cQ), blo, bhi, wl, wh, Pl, Ph, Ql,
+                     Qh);
+}
+template <typename T>
+__device__ __forceinline__ void reconstruct_tail(T w0, T sw, T P0, T sP, T Q0, T sQ, T blo, T bhi,
+                                                 T &wl, T &wh, T &Pl, T &Ph, T &Ql, T &Qh)
+{
     T a = w0 + (T)0.5 * sw, b = w0 - (T)0.5 * sw;
     // positivity: a face value below the face bed is raised to it and the
     // other face value mirrored about w0 (selects, no branches)
@@ -781,11 +803,11 @@ __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
 
 template <typename T>
-__device__ __forceinline__ FaceSt<T> face_state(T wf, T Pf, T Qf, T bf, T g, T sqrtg, T eps)
+__device__ __forceinline__ FaceSt<T> face_state(T wf, T Pf, T Qf, T bf, T g, T sqrtg, T eps, T hdry)
 {
     FaceSt<T> s;
     s.h = tmax(wf - bf, (T)0);
-    const IvC<T> ic = ivc(s.h, g, sqrtg, eps);
+    const IvC<T> ic = ivc(s.h, g, sqrtg, eps, hdry);
     s.u = ic.iv * Pf;
     s.v = ic.iv * Qf;
     s.c = ic.c;
@@ -852,7 +874,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     const int kc = min(i, nx + 2), kc1 = min(i + 1, nx + 2);
     const bool lane_out = lane >= 2 && lane <= 29 && i < nx;
     const T *w = D.w[cf.wc];
-    const T g = D.g, eps = D.eps, th = THETA1 ? (T)1 : D.theta, sqrtg = tsqrt(g);
+    const T g = D.g, eps = D.eps, hdry = D.hdry, th = THETA1 ? (T)1 : D.theta, sqrtg = tsqrt(g);
     const T rdx = D.rdx, rdy = D.rdy, half_rdx = (T)0.5 * rdx, half_rdy = (T)0.5 * rdy;
     const T rdx2 = rdx * rdx, rdy2 = rdy * rdy, q_rdxy = (T)0.25 * rdx * rdy;
     const T c_xxx = (T)0.5 * rdx2 * rdx, c_yyy = (T)0.5 * rdy2 * rdy;
@@ -873,6 +895,11 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     T KW[4] = {0, 0, 0, 0}, KRW[4] = {0, 0, 0, 0};  // corners at columns i and i+1, rows r-2..r+1
     FaceSt<T> Nprev = {0, 0, 0, 0};                  // N face state of row r-2
     T Hy0 = 0, Hy1 = 0, Hy2 = 0;                     // y-flux below row r-2 (face (r-2)-1/2)
+    // passed on from the previous step: the y-differences q(r-1) - q(r-2) of
+    // w, P, Q (the backward differences of this step's y-reconstruction), and
+    // the face beds of the S and N faces of the previous reconstructed row
+    // (this row's S face and the source's S face)
+    T ayw = 0, ayP = 0, ayQ = 0, bSc = 0, bNc = 0;
     {
         int rr = min(j0 - 2, ny + 2);
         KW[3] = corner[(long long)(rr + 2) * cp + (kc + 2)];
@@ -957,25 +984,42 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
         // ---- y-reconstruction of row r-1 (rows r-2, r-1, r) and the y-face flux
         //      between rows r-2 and r-1
         {
-            T bS = (T)0.5 * (KW[1] + KRW[1]), bN = (T)0.5 * (KW[2] + KRW[2]);
+            const T bS = bNc, bN = (T)0.5 * (KW[2] + KRW[2]);
+            const T bS0 = bSc, bN0 = bS;  // faces of the output row o = r - 2
+            bSc = bS;
+            bNc = bN;
             T wl, wh, Pl, Ph, Ql, Qh;
-            reconstruct(wW[1], wW[2], wW[3], PW[1], PW[2], PW[3], QW[1], QW[2], QW[3], bS, bN, th,
-                        wl, wh, Pl, Ph, Ql, Qh);
-            FaceSt<T> S = face_state(wl, Pl, Ql, bS, g, sqrtg, eps);
-            FaceSt<T> Nn = face_state(wh, Ph, Qh, bN, g, sqrtg, eps);
+            if (THETA1) {
+                const T cw = wW[3] - wW[2], cP = PW[3] - PW[2], cQ = QW[3] - QW[2];
+                reconstruct_d(wW[2], ayw, cw, PW[2], ayP, cP, QW[2], ayQ, cQ, bS, bN, wl, wh, Pl, Ph, Ql, Qh);
+                ayw = cw; ayP = cP; ayQ = cQ;
+            } else {
+                reconstruct(wW[1], wW[2], wW[3], PW[1], PW[2], PW[3], QW[1], QW[2], QW[3], bS, bN, th,
+                            wl, wh, Pl, Ph, Ql, Qh);
+            }
+            FaceSt<T> S = face_state(wl, Pl, Ql, bS, g, sqrtg, eps, hdry);
+            FaceSt<T> Nn = face_state(wh, Ph, Qh, bN, g, sqrtg, eps, hdry);
             T h0, h1, h2;
             cu_flux_st<T, 1>(Nprev, S, g, h0, h1, h2);  // face (r-1)-1/2 = o+1/2 for o = r-2
             // ---- finish row o = r - 2
             const int o = r - 2;
             // x-reconstruction of row o needs w, P, Q of the lanes next door
+            // (lane 31 takes its own values where the lane to the right would
+            // give them; nothing of lane 31 reaches an output lane)
             T w0 = wW[1], P0 = PW[1], Q0 = QW[1];
-            T wm = shup(w0, 1), wp = shdn(w0, 1), Pm = shup(P0, 1), Pp = shdn(P0, 1);
+            T wp = shdn(w0, 1), Pm = shup(P0, 1), Pp = shdn(P0, 1);
             T Qm = shup(Q0, 1), Qp = shdn(Q0, 1);
-            T bxW = (T)0.5 * (KW[0] + KW[1]), bxE = (T)0.5 * (KRW[0] + KRW[1]);
+            const T bxW = (T)0.5 * (KW[0] + KW[1]), bxE = shdn(bxW, 1);  // the E face is the next W face
             T xwl, xwh, xPl, xPh, xQl, xQh;
-            reconstruct(wm, w0, wp, Pm, P0, Pp, Qm, Q0, Qp, bxW, bxE, th, xwl, xwh, xPl, xPh, xQl, xQh);
-            FaceSt<T> Wst = face_state(xwl, xPl, xQl, bxW, g, sqrtg, eps);
-            FaceSt<T> Est = face_state(xwh, xPh, xQh, bxE, g, sqrtg, eps);
+            if (THETA1) {
+                const T cw = wp - w0, cP = Pp - P0, cQ = Qp - Q0;
+                reconstruct_d(w0, shup(cw, 1), cw, P0, shup(cP, 1), cP, Q0, shup(cQ, 1), cQ, bxW, bxE, xwl, xwh, xPl,
+                              xPh, xQl, xQh);
+            } else {
+                reconstruct(shup(w0, 1), w0, wp, Pm, P0, Pp, Qm, Q0, Qp, bxW, bxE, th, xwl, xwh, xPl, xPh, xQl, xQh);
+            }
+            FaceSt<T> Wst = face_state(xwl, xPl, xQl, bxW, g, sqrtg, eps, hdry);
+            FaceSt<T> Est = face_state(xwh, xPh, xQh, bxE, g, sqrtg, eps, hdry);
             FaceSt<T> El;  // E state of the lane to the left
             El.h = shup(Est.h, 1); El.u = shup(Est.u, 1); El.v = shup(Est.v, 1); El.c = shup(Est.c, 1);
             T x0, x1, x2;
@@ -992,7 +1036,6 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 const long long c = fidx(D, i, o);
                 T divx0 = (xe0 - x0) * rdx, divx1 = (xe1 - x1) * rdx, divx2 = (xe2 - x2) * rdx;
                 T divy0 = (h0 - Hy0) * rdy, divy1 = (h1 - Hy1) * rdy, divy2 = (h2 - Hy2) * rdy;
-                T bS0 = (T)0.5 * (KW[0] + KRW[0]), bN0 = (T)0.5 * (KW[1] + KRW[1]);
                 T bc = bW[0];
                 T srcx = -g * (bxE - bxW) * rdx * (w0 - (T)0.5 * (bxE + bxW));
                 T srcy = -g * (bN0 - bS0) * rdy * (w0 - (T)0.5 * (bN0 + bS0));
@@ -2005,7 +2048,7 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         Pv[q] = Pn;
         cPv[q] = cn;
         T h = tmax(wq - bv[q], (T)0);
-        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
         T u = ic.iv * Pn, v = ic.iv * Qv[q];
         T cc = ic.c;
         rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
@@ -2299,7 +2342,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             Pv[q] = Pn;
             cPv[q] = cn;
             T h = tmax(wq - bv[q], (T)0);
-            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
@@ -2507,7 +2550,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             Pv[q] = Pn;
             cPv[q] = cn;
             T h = tmax(wq - bv[q], (T)0);
-            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+            const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
             rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
@@ -2925,7 +2968,7 @@ __global__ void __launch_bounds__(256) k_rate(Dev<T> D, int wc)
         int i = (int)(q % D.nx), j = (int)(q / D.nx);
         long long c = fidx(D, i, j);
         T h = tmax(w[c] - D.bC[c], (T)0);
-        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps);
+        const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
         T u = ic.iv * D.P[c], v = ic.iv * D.Q[c];
         T cc = ic.c;
         T r = tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy);
@@ -3115,15 +3158,25 @@ static bool rhs_pair(const Dev<T> &D)
 // one wave: 2048 x 2048 and up) the paired kernel takes 64; on smaller grids
 // the multiple of the y-chunk rows in {64, 48, 32, 24, 16} that minimises the
 // estimate (24 at 1000 x 1500, 16 below a million cells).  The one-column
-// kernels are compiled for 16, 32 and 64 rows and take 64, or 32 when 64-row
-// strips give fewer than four warps per multiprocessor.
+// kernels are compiled for 16, 32 and 64 rows (and 128 with the chunk
+// summaries of 8 rows) and take 64, or 32 when 64-row strips give fewer than
+// four warps per multiprocessor; in double precision 128 where 128-row strips
+// still give seven warps per multiprocessor (2048 x 2048).
 template <typename T>
 static int rhs_rows(const Dev<T> &D)
 {
     const bool pair = rhs_pair(D);
+    // 128 rows: the one-column kernel that forms the chunk summaries only
+    const bool r128 = !pair && rhs_fast(D) && D.tune_ysum == 0 && ysplit_rows<T>(D.tune_yk) == 8;
+    if (D.tune_rows == 128) return r128 ? 128 : 64;
     if (D.tune_rows > 0) return pair || D.tune_rows == 16 || D.tune_rows == 64 ? D.tune_rows : 32;
     if (!pair) {
-        const long long warps64 = (long long)((D.nx + SW_COLS - 1) / SW_COLS) * ((D.ny + 63) / 64);
+        const long long nstrip = (D.nx + SW_COLS - 1) / SW_COLS;
+        // double precision on large grids: 128-row strips (4 halo rows in 132
+        // against 4 in 68; the kernel is bound by the FP64 pipe, which two
+        // warps per scheduler keep busy)
+        if (sizeof(T) == 8 && r128 && nstrip * ((D.ny + 127) / 128) >= 7LL * D.nsm) return 128;
+        const long long warps64 = nstrip * ((D.ny + 63) / 64);
         return warps64 >= 4LL * D.nsm ? 64 : 32;
     }
     const int ky = ysplit_rows<T>(D.tune_yk);
@@ -3188,6 +3241,8 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         if (rows == 32) {
             if (KY == 16) k_rhs_sw<T, 32, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
             else k_rhs_sw<T, 32, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
+        } else if (rows == 128) {
+            k_rhs_sw<T, 128, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);
         } else {
             if (KY == 16) k_rhs_sw<T, 64, true, true, 16><<<blocks, 128, 0, st>>>(D, nstrip);
             else k_rhs_sw<T, 64, true, true, 8><<<blocks, 128, 0, st>>>(D, nstrip);

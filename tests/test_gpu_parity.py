@@ -312,7 +312,8 @@ def test_bounded_wait_times_out():
 @pytest.mark.parametrize("tune", [(0, 0, 2, 0), (0, 0, 2, 0, 16), (0, 0, 8, 0, 4), (0, 0, 8, 0, 8), (0, 0, 0, 0, 4),
                                   (0, 0, 16, 0, 4), (0, 0, 16, 0, 8), (0, 0, 0, 0, 0, 0, 1), (0, 0, 0, 32, 0, 16),
                                   (0, 0, 0, 0, 0, 0, 2), (0, 0, 0, 32, 0, 0, 3), (0, 0, 0, 16),
-                                  (0, 0, 0, 24), (0, 0, 0, 48), (0, 0, 0, 24, 0, 16), (0, 0, 0, 64)])
+                                  (0, 0, 0, 24), (0, 0, 0, 48), (0, 0, 0, 24, 0, 16), (0, 0, 0, 64),
+                                  (0, 0, 0, 128)])
 def test_kernel_variants_match_oracle(tune):
     # every kernel shape (paired or one-column RHS and its rows per warp,
     # warp-per-row, persistent staged or register x-solver and its elements
