@@ -76,6 +76,9 @@ struct Dev {
     T *bC;                    // bed at cell centres (padded field, halo included)
     T *fxm, *fxe, *fxc;       // x-line Thomas factors: m, -a m, c m
     T *fym, *fye, *fyc;       // y-line Thomas factors
+    // double precision: the F*, G* coefficients of Eqs. 14-15 at the cell
+    // centres, d d_x / 6, d d_y / 6 and (B + 1/3) d^2 (null in single precision)
+    T *fsc1, *fsc2, *fsc3;
     T *gx, *gy;               // sponge factor profiles along x and y (product of sides)
     const double *cW, *cE, *cS, *cN;  // raw boundary coefficients for maker rows
     T *corrW, *corrE, *corrS, *corrN; // per-step maker corrections of the line right-hand sides

@@ -1074,8 +1074,15 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 T P_x = (Pp - Pm) * half_rdx;
                 T P_y = (PW[2] - PW[0]) * half_rdy;
                 T P_xy = (PNp - PSp - PNm + PSm) * q_rdxy;
-                T Fs = d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
-                T Gs = d * ddy * P_x * sixth + d * ddx * P_y * sixth + kB * d * d * P_xy;
+                T Fs, Gs;
+                if constexpr (sizeof(T) == 8) {
+                    const T c1 = D.fsc1[c], c2 = D.fsc2[c], c3 = D.fsc3[c];
+                    Fs = c1 * Q_y + c2 * Q_x + c3 * Q_xy;
+                    Gs = c2 * P_x + c1 * P_y + c3 * P_xy;
+                } else {
+                    Fs = d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+                    Gs = d * ddy * P_x * sixth + d * ddx * P_y * sixth + kB * d * d * P_xy;
+                }
                 // AB3 / Euler combine (Eqs. 42-43), history prefetched one step ahead
                 T dw = b0c * E, dU = b0c * F, dV = b0c * G + g0c * Gs;
                 if (extrap) dU += g0c * Fs;
@@ -1905,7 +1912,26 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
     vload_k<T, K>(D.dU + rowo + ib, r);
     vload_k<T, K>(D.fxm + rowo + ib, m);
     vload_k<T, K>(D.fxe + rowo + ib, e);
-    if (seq) {
+    if (seq && sizeof(T) == 8) {
+        // F* of Eq. 14 at the new level from Q^{n+1} (ghosts at t_{n+1}),
+        // with the coefficients formed at set-up
+        const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
+        T c1[K], c2[K], c3[K];
+        vload_k<T, K>(D.fsc1 + rowo + ib, c1);
+        vload_k<T, K>(D.fsc2 + rowo + ib, c2);
+        vload_k<T, K>(D.fsc3 + rowo + ib, c3);
+        T q0[K + 2], qm[K + 2], qp[K + 2];
+        load_halo_chunk<T, K>(D.Q + rowo, ib, lane, q0);
+        load_halo_chunk<T, K>(D.Q + rowo - D.pitch, ib, lane, qm);
+        load_halo_chunk<T, K>(D.Q + rowo + D.pitch, ib, lane, qp);
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            T Q_x = (q0[q + 2] - q0[q]) * half_rdx;
+            T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
+            T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
+            r[q] += c1[q] * Q_y + c2[q] * Q_x + c3[q] * Q_xy;
+        }
+    } else if (seq) {
         // F* of Eq. 14 at the new level from Q^{n+1} (ghosts at t_{n+1})
         const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy, q_rdxy = (T)0.25 * D.rdx * D.rdy;
         const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
@@ -2672,6 +2698,32 @@ __global__ void k_setup_centres(Dev<T> D, SetupArgs A)
     }
 }
 
+// Double precision: the F*, G* coefficients of Eqs. 14-15 at the interior
+// cell centres from the still depth d and its central differences d_x, d_y
+// (as the step kernels form them): F* = c1 Q_y + c2 Q_x + c3 Q_xy and
+// G* = c2 P_x + c1 P_y + c3 P_xy with c1 = d d_x / 6, c2 = d d_y / 6,
+// c3 = (B + 1/3) d^2.  At GB300's FP64 rate a load is cheaper than the dozen
+// operations that form them in every step.
+template <typename T>
+__global__ void k_setup_fstar(Dev<T> D)
+{
+    const int nx = D.nx;
+    const long long n = (long long)nx * D.ny;
+    const T half_rdx = (T)0.5 * D.rdx, half_rdy = (T)0.5 * D.rdy;
+    const T kB = D.Bd + (T)1 / (T)3, sixth = (T)1 / (T)6;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nx), j = (int)(q / nx);
+        auto dep = [&](int a, int b) { return tmax(D.w_s - D.bC[fidx(D, a, b)], (T)0); };
+        const T d = dep(i, j);
+        const T ddx = (dep(i + 1, j) - dep(i - 1, j)) * half_rdx;
+        const T ddy = (dep(i, j + 1) - dep(i, j - 1)) * half_rdy;
+        const long long c = fidx(D, i, j);
+        D.fsc1[c] = d * ddx * sixth;
+        D.fsc2[c] = d * ddy * sixth;
+        D.fsc3[c] = kB * d * d;
+    }
+}
+
 // Thomas factors (m, -a m, c' = c m) of every x-line and y-line, boundary
 // rows closed: wall or sponge = odd mirror of the normal flux (the outside
 // coefficient moves onto the diagonal), maker = the outside value is known
@@ -2883,6 +2935,7 @@ cudaError_t launch_setup(const Dev<T> &D, cudaStream_t st, const SetupArgs &A)
     cudaError_t e = cudaFuncSetAttribute(k_setup_factors<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
     if (e != cudaSuccess) return e;
     k_setup_factors<T><<<(D.ny + 31) / 32 + (D.nx + 31) / 32, 32 * FS_SEG, fsm, st>>>(D, A);
+    if constexpr (sizeof(T) == 8) k_setup_fstar<T><<<gs, 256, 0, st>>>(D);
     k_setup_state<T><<<gs, 256, 0, st>>>(D, A);
     return cudaGetLastError();
 }
