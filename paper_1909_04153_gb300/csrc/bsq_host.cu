@@ -164,7 +164,7 @@ static Layout layout(int nx, int ny, int tune_xk, bool kahan, int nc)
     const long long fs = (long long)pitch * (ny + 4);
     L.fb = align256((size_t)fs * sizeof(T));
     const int nstate = kahan ? 7 : 4;  // w0, w1, P, Q (+ cw, cP, cQ)
-    L.nfields = nstate + 15 + 2 + 1 + 6 + (sizeof(T) == 8 ? 3 : 0);
+    L.nfields = nstate + 15 + 2 + 1 + 6 + (sizeof(T) == 8 ? 3 + ST_N : 0);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     L.o_fields = take(L.fb * L.nfields);
@@ -362,8 +362,15 @@ static bsq_status create_T(bsq_domain *dm, const double *bed, const double *eta0
     D.bC = field(k++);
     D.fxm = field(k++); D.fxe = field(k++); D.fxc = field(k++);
     D.fym = field(k++); D.fye = field(k++); D.fyc = field(k++);
-    if (sizeof(T) == 8) { D.fsc1 = field(k++); D.fsc2 = field(k++); D.fsc3 = field(k++); }
-    else { D.fsc1 = D.fsc2 = D.fsc3 = nullptr; }
+    if (sizeof(T) == 8) {
+        D.fsc1 = field(k++); D.fsc2 = field(k++); D.fsc3 = field(k++);
+        D.stat = field(k); k += ST_N;
+        D.stat_stride = (long long)(fb / sizeof(T));
+    } else {
+        D.fsc1 = D.fsc2 = D.fsc3 = nullptr;
+        D.stat = nullptr;
+        D.stat_stride = 0;
+    }
     D.corner = (T *)(base + o_corner);
     D.cpitch = cx;
     D.gx = (T *)(base + o_gx);

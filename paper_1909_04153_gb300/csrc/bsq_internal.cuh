@@ -42,6 +42,13 @@ struct Coef {
     float betaf[3], gamf[3];
 };
 
+// Static terms of the double-precision RHS (Eqs. 11-13), formed at set-up from
+// the corner bed and the still depth exactly as the kernel formed them:
+// bed-slope source -g (b_E - b_W) / dx and the face-bed mean (b_E + b_W) / 2 in
+// x, the same in y, and for the dispersive terms B g d^2, B g d^3 and the
+// central differences d_x, d_y of the still depth.
+enum { ST_SX = 0, ST_MX, ST_SY, ST_MY, ST_BD2, ST_BD3, ST_DDX, ST_DDY, ST_N };
+
 // Everything a kernel needs, passed by value.  T = float or double.
 template <typename T>
 struct Dev {
@@ -79,6 +86,10 @@ struct Dev {
     // double precision: the F*, G* coefficients of Eqs. 14-15 at the cell
     // centres, d d_x / 6, d d_y / 6 and (B + 1/3) d^2 (null in single precision)
     T *fsc1, *fsc2, *fsc3;
+    // double precision: further static terms of the RHS at the cell centres,
+    // field k at stat + k stat_stride (ST_*; null in single precision)
+    T *stat;
+    long long stat_stride;
     T *gx, *gy;               // sponge factor profiles along x and y (product of sides)
     const double *cW, *cE, *cS, *cN;  // raw boundary coefficients for maker rows
     T *corrW, *corrE, *corrS, *corrN; // per-step maker corrections of the line right-hand sides

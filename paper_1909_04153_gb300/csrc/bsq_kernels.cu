@@ -1037,8 +1037,19 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 T divx0 = (xe0 - x0) * rdx, divx1 = (xe1 - x1) * rdx, divx2 = (xe2 - x2) * rdx;
                 T divy0 = (h0 - Hy0) * rdy, divy1 = (h1 - Hy1) * rdy, divy2 = (h2 - Hy2) * rdy;
                 T bc = bW[0];
-                T srcx = -g * (bxE - bxW) * rdx * (w0 - (T)0.5 * (bxE + bxW));
-                T srcy = -g * (bN0 - bS0) * rdy * (w0 - (T)0.5 * (bN0 + bS0));
+                // double precision reads the static terms set-up formed in the
+                // same order of operations (the same values, bitwise)
+                constexpr bool STAT = sizeof(T) == 8;
+                const T *st = STAT ? D.stat + c : nullptr;
+                const long long ss = STAT ? D.stat_stride : 0;
+                T srcx, srcy;
+                if constexpr (STAT) {
+                    srcx = st[ST_SX * ss] * (w0 - st[ST_MX * ss]);
+                    srcy = st[ST_SY * ss] * (w0 - st[ST_MY * ss]);
+                } else {
+                    srcx = -g * (bxE - bxW) * rdx * (w0 - (T)0.5 * (bxE + bxW));
+                    srcy = -g * (bN0 - bS0) * rdy * (w0 - (T)0.5 * (bN0 + bS0));
+                }
                 T fr1 = (T)0, fr2 = (T)0;
                 if (!FAST && D.friction != (T)0) {
                     T h = tmax(w0 - bc, (T)0);
@@ -1049,8 +1060,18 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                     fr2 = D.friction * v * sp;
                 }
                 const T d = dW[1];
-                const T ddx = (dp - dm) * half_rdx;
-                const T ddy = (dW[2] - dW[0]) * half_rdy;
+                T ddx, ddy, Bd2, Bd3;  // d_x, d_y, B g d^2, B g d^3
+                if constexpr (STAT) {
+                    ddx = st[ST_DDX * ss];
+                    ddy = st[ST_DDY * ss];
+                    Bd2 = st[ST_BD2 * ss];
+                    Bd3 = st[ST_BD3 * ss];
+                } else {
+                    ddx = (dp - dm) * half_rdx;
+                    ddy = (dW[2] - dW[0]) * half_rdy;
+                    Bd2 = Bg * d * d;
+                    Bd3 = Bd2 * d;
+                }
                 const T e0 = eW[2];
                 T e_xx = (ep1 - (T)2 * e0 + em1) * rdx2;
                 T e_yy = (eW[3] - (T)2 * e0 + eW[1]) * rdy2;
@@ -1063,8 +1084,8 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 T exx_m = (eSp - (T)2 * eW[1] + eSm) * rdx2;
                 T e_xyy = (eyy_p - eyy_m) * half_rdx;
                 T e_xxy = (exx_p - exx_m) * half_rdy;
-                T dispx = Bg * d * d * d * (e_xxx + e_xyy) + Bg * d * d * (ddx * ((T)2 * e_xx + e_yy) + ddy * e_xy);
-                T dispy = Bg * d * d * d * (e_yyy + e_xxy) + Bg * d * d * (ddy * ((T)2 * e_yy + e_xx) + ddx * e_xy);
+                T dispx = Bd3 * (e_xxx + e_xyy) + Bd2 * (ddx * ((T)2 * e_xx + e_yy) + ddy * e_xy);
+                T dispy = Bd3 * (e_yyy + e_xxy) + Bd2 * (ddy * ((T)2 * e_yy + e_xx) + ddx * e_xy);
                 T E = -divx0 - divy0;
                 T F = -divx1 - divy1 + srcx - fr1 + dispx;
                 T G = -divx2 - divy2 + srcy - fr2 + dispy;
@@ -2721,6 +2742,24 @@ __global__ void k_setup_fstar(Dev<T> D)
         D.fsc1[c] = d * ddx * sixth;
         D.fsc2[c] = d * ddy * sixth;
         D.fsc3[c] = kB * d * d;
+        // the RHS kernel's other static terms, in its order of operations
+        const T *kc = D.corner;
+        const int cp = D.cpitch;
+        auto K = [&](int a, int b) { return kc[(long long)(b + 2) * cp + (a + 2)]; };
+        const T bxW = (T)0.5 * (K(i, j) + K(i, j + 1)), bxE = (T)0.5 * (K(i + 1, j) + K(i + 1, j + 1));
+        const T bS = (T)0.5 * (K(i, j) + K(i + 1, j)), bN = (T)0.5 * (K(i, j + 1) + K(i + 1, j + 1));
+        const T g = D.g, Bg = D.Bd * g;
+        T *st = D.stat + c;
+        const long long ss = D.stat_stride;
+        st[ST_SX * ss] = -g * (bxE - bxW) * D.rdx;
+        st[ST_MX * ss] = (T)0.5 * (bxE + bxW);
+        st[ST_SY * ss] = -g * (bN - bS) * D.rdy;
+        st[ST_MY * ss] = (T)0.5 * (bN + bS);
+        const T bd2 = Bg * d * d;
+        st[ST_BD2 * ss] = bd2;
+        st[ST_BD3 * ss] = bd2 * d;
+        st[ST_DDX * ss] = ddx;
+        st[ST_DDY * ss] = ddy;
     }
 }
 
