@@ -900,6 +900,9 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
     // the face beds of the S and N faces of the previous reconstructed row
     // (this row's S face and the source's S face)
     T ayw = 0, ayP = 0, ayQ = 0, bSc = 0, bNc = 0;
+    // eta_xx of the output row and the row below it, formed one and two steps
+    // earlier as the eta_xx of the row above the output row
+    T exx0 = 0, exx1 = 0;
     {
         int rr = min(j0 - 2, ny + 2);
         KW[3] = corner[(long long)(rr + 2) * cp + (kc + 2)];
@@ -1073,15 +1076,18 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                     Bd3 = Bd2 * d;
                 }
                 const T e0 = eW[2];
-                T e_xx = (ep1 - (T)2 * e0 + em1) * rdx2;
+                // eta_xx of rows o-1, o, o+1: two passed on, one new; eta_yy of
+                // the lanes next door by shuffles (the same expressions, so the
+                // same values)
+                const T exx_p = (eNp - (T)2 * eW[3] + eNm) * rdx2;
+                const T e_xx = exx0, exx_m = exx1;
+                exx1 = exx0;
+                exx0 = exx_p;
                 T e_yy = (eW[3] - (T)2 * e0 + eW[1]) * rdy2;
                 T e_xy = (eNp - eSp - eNm + eSm) * q_rdxy;
                 T e_xxx = (ep2 - (T)2 * ep1 + (T)2 * em1 - em2) * c_xxx;
                 T e_yyy = (eW[4] - (T)2 * eW[3] + (T)2 * eW[1] - eW[0]) * c_yyy;
-                T eyy_p = (eNp - (T)2 * ep1 + eSp) * rdy2;
-                T eyy_m = (eNm - (T)2 * em1 + eSm) * rdy2;
-                T exx_p = (eNp - (T)2 * eW[3] + eNm) * rdx2;
-                T exx_m = (eSp - (T)2 * eW[1] + eSm) * rdx2;
+                const T eyy_p = shdn(e_yy, 1), eyy_m = shup(e_yy, 1);
                 T e_xyy = (eyy_p - eyy_m) * half_rdx;
                 T e_xxy = (exx_p - exx_m) * half_rdy;
                 T dispx = Bd3 * (e_xxx + e_xyy) + Bd2 * (ddx * ((T)2 * e_xx + e_yy) + ddy * e_xy);
