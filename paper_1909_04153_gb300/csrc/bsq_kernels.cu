@@ -1866,8 +1866,12 @@ __device__ __forceinline__ void yapply_body(const Dev<T> &D, int bx, int by, int
             Qn = Qo[q] + x;
         }
         const int j = j0 + q;
-        T gm = gxi * D.gy[min(j, ny - 1)];
-        if (tlt(gm, (T)1)) { Qn *= gm; cn *= gm; }
+        const T gyq = D.gy[min(j, ny - 1)];
+        if (tlt(gxi, (T)1) || tlt(gyq, (T)1)) {  // the product of factors in [0, 1] is below 1
+            const T gm = gxi * gyq;
+            Qn *= gm;
+            cn *= gm;
+        }
         Qo[q] = Qn;
         cq[q] = cn;
     }
@@ -2074,7 +2078,7 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
     vload_k<T, K>(D.Q + rowo + ib, Qv);
     vload_k<T, K>(D.bC + rowo + ib, bv);
     const T gyj = D.gy[j];
-    T rate = (T)0;
+    T mu = (T)0, mv = (T)0;  // largest |u| + c and |v| + c (Eq. 22), scaled once
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < K; q++) {
@@ -2089,8 +2093,9 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
             Pn = Pv[q] + r[q];
         }
         T wq = wv[q];
-        T gm = D.gx[i] * gyj;
-        if (tlt(gm, (T)1)) {
+        const T gxi = D.gx[i];
+        if (tlt(gxi, (T)1) || tlt(gyj, (T)1)) {  // the product of factors in [0, 1] is below 1
+            const T gm = gxi * gyj;
             T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
             wq = bv[q] + (d + gm * (h - d));
             wr[i] = wq;
@@ -2104,13 +2109,14 @@ __global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
         const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
         T u = ic.iv * Pn, v = ic.iv * Qv[q];
         T cc = ic.c;
-        rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+        mu = tmax(mu, fabs(u) + cc);
+        mv = tmax(mv, fabs(v) + cc);
         if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
     }
     vstore_k<T, K>(Pr + ib, Pv);
     if (D.kahan) vstore_k<T, K>(cPr + ib, cPv);
 
-    double rr = (double)rate;
+    double rr = (double)tmax(mu * D.rdx, mv * D.rdy);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
     bool anybad = __any_sync(0xffffffffu, bad);
@@ -2238,7 +2244,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         if ((int)blockIdx.x < ny) xrow_issue(D, cf, blockIdx.x, buf0, span, &bar[0]);
     }
     __syncthreads();
-    T rate = (T)0;
+    T mu = (T)0, mv = (T)0;  // largest |u| + c and |v| + c (Eq. 22), scaled once
     bool bad = false, failed = false;
     int it = 0;
     for (int j = blockIdx.x; j < ny; j += gridDim.x, it++) {
@@ -2383,8 +2389,9 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
                 Pn = Pv[q] + r[q];
             }
             T wq = wv[q];
-            T gm = D.gx[i] * gyj;
-            if (tlt(gm, (T)1)) {
+            const T gxi = D.gx[i];
+            if (tlt(gxi, (T)1) || tlt(gyj, (T)1)) {  // the product of factors in [0, 1] is below 1
+                const T gm = gxi * gyj;
                 T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
                 wq = bv[q] + (d + gm * (h - d));
                 wrow[i] = wq;
@@ -2398,7 +2405,8 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
             const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
-            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+            mu = tmax(mu, fabs(u) + cc);
+            mv = tmax(mv, fabs(v) + cc);
             if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
         }
         if (ib < nx) {
@@ -2418,7 +2426,7 @@ __global__ void __launch_bounds__(512, 1) k_xsolve_pipe(Dev<T> D, int span, doub
         }
         return;
     }
-    double rr = (double)rate;
+    double rr = (double)tmax(mu * D.rdx, mv * D.rdy);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
     bool anybad = __any_sync(0xffffffffu, bad);
@@ -2453,6 +2461,9 @@ template <typename T, int K, bool FIXED = false>
 __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf, int j, T *ys, T &rate, bool &bad)
 {
     const int lane = threadIdx.x & 31;
+    // largest |u| + c and |v| + c of Eq. 22 over the lane's cells, scaled once at the
+    // end (scaling by a positive constant keeps the order, so the largest rate)
+    T mu = (T)0, mv = (T)0;
     const int nx = D.nx, ny = D.ny;
     const bool seq = FIXED || D.cross_mode != 0;
     const bool kah = FIXED || D.kahan != 0;
@@ -2473,13 +2484,23 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
         vload_k_if<T, K>(act, D.fxm + rowo + ib, m);
         vload_k_if<T, K>(act, D.fxe + rowo + ib, e);
         if (seq) {
-            T Qc[K + 2], bc_[K + 2], qm[K + 2], qp[K + 2], bm[K], bp[K];
+            // double precision: the F* coefficients formed at set-up;
+            // single precision: the still depth from the bed rows
+            constexpr bool F64 = sizeof(T) == 8;
+            T Qc[K + 2], bc_[F64 ? 1 : K + 2], qm[K + 2], qp[K + 2], bm[F64 ? 1 : K], bp[F64 ? 1 : K];
+            T c1[F64 ? K : 1], c2[F64 ? K : 1], c3[F64 ? K : 1];
             load_halo_chunk_if<T, K>(act, Qr, ib, lane, Qc);
-            load_halo_chunk_if<T, K>(act, br, ib, lane, bc_);
             load_halo_chunk_if<T, K>(act, Qr - D.pitch, ib, lane, qm);
             load_halo_chunk_if<T, K>(act, Qr + D.pitch, ib, lane, qp);
-            vload_k_if<T, K>(act, br - D.pitch + ib, bm);
-            vload_k_if<T, K>(act, br + D.pitch + ib, bp);
+            if constexpr (F64) {
+                vload_k_if<T, K>(act, D.fsc1 + rowo + ib, c1);
+                vload_k_if<T, K>(act, D.fsc2 + rowo + ib, c2);
+                vload_k_if<T, K>(act, D.fsc3 + rowo + ib, c3);
+            } else {
+                load_halo_chunk_if<T, K>(act, br, ib, lane, bc_);
+                vload_k_if<T, K>(act, br - D.pitch + ib, bm);
+                vload_k_if<T, K>(act, br + D.pitch + ib, bp);
+            }
             // ghosts of Q^{n+1} at t_{n+1}, as in k_xsolve_pipe
             if (ib == 0) {
                 if (j - 1 >= 0) qm[0] = D.bc[SW] == MAKER ? D.mqW[j - 1] : qm[1];
@@ -2509,13 +2530,17 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             }
 #pragma unroll
             for (int q = 0; q < K; q++) {
-                T d = tmax(D.w_s - bc_[q + 1], (T)0);
-                T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
-                T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
                 T Q_x = (Qc[q + 2] - Qc[q]) * half_rdx;
                 T Q_y = (qp[q + 1] - qm[q + 1]) * half_rdy;
                 T Q_xy = (qp[q + 2] - qm[q + 2] - qp[q] + qm[q]) * q_rdxy;
-                r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+                if constexpr (F64) {
+                    r[q] += c1[q] * Q_y + c2[q] * Q_x + c3[q] * Q_xy;
+                } else {
+                    T d = tmax(D.w_s - bc_[q + 1], (T)0);
+                    T ddx = (tmax(D.w_s - bc_[q + 2], (T)0) - tmax(D.w_s - bc_[q], (T)0)) * half_rdx;
+                    T ddy = (tmax(D.w_s - bp[q], (T)0) - tmax(D.w_s - bm[q], (T)0)) * half_rdy;
+                    r[q] += d * ddx * Q_y * sixth + d * ddy * Q_x * sixth + kB * d * d * Q_xy;
+                }
             }
         }
 #pragma unroll
@@ -2591,8 +2616,8 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
                 Pn = Pv[q] + x[q];
             }
             T wq = wv[q];
-            T gm = gxv[q] * gyj;
-            if (tlt(gm, (T)1)) {
+            if (tlt(gxv[q], (T)1) || tlt(gyj, (T)1)) {  // the product of factors in [0, 1] is below 1
+                const T gm = gxv[q] * gyj;
                 T h = tmax(wq - bv[q], (T)0), d = tmax(D.w_s - bv[q], (T)0);
                 wq = bv[q] + (d + gm * (h - d));
                 wrow[i] = wq;
@@ -2606,7 +2631,8 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             const IvC<T> ic = ivc(h, D.g, tsqrt(D.g), D.eps, D.hdry);
             T u = ic.iv * Pn, v = ic.iv * Qv[q];
             T cc = ic.c;
-            rate = tmax(rate, tmax((fabs(u) + cc) * D.rdx, (fabs(v) + cc) * D.rdy));
+            mu = tmax(mu, fabs(u) + cc);
+            mv = tmax(mv, fabs(v) + cc);
             if (!tfinite(wq) || !tfinite(Pn) || !tfinite(Qv[q])) bad = true;
         }
         if (ib < nx) {
@@ -2614,6 +2640,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
             if (kah) vstore_k<T, K>(cPr + ib, cPv);
         }
     }
+    rate = tmax(rate, tmax(mu * D.rdx, mv * D.rdy));
 }
 
 constexpr int XW_WARPS = 4;  // rows (warps) per block of the warp-per-row x-solver
