@@ -252,6 +252,31 @@ def test_gpu_mass_conservation_fp64():
         assert abs(info["mass"] - m0) <= 1e-12 * m0
 
 
+@pytest.mark.parametrize("nx,ny", [(16384, 4), (4, 16384)])
+def test_longest_lines_match_oracle(nx, ny):
+    # the largest side bsq_create accepts: rows of 16384 cells take the x-solver
+    # with 32 elements a thread (registers only), columns of 16384 cells a y-line
+    # chunk scan of eight passes
+    # The long rows carry a discharge ~1e4 times the cross-line one, so the
+    # fluxes are held as one vector field (P, Q): the cross-line flux's own
+    # norm would weigh round-off of the large terms 1e4 times over.
+    case = _hump_case(nx, ny, dx=0.05, seed=29)
+    o = _oracle(case)
+    dts = o.run(20)
+    with bsq.Domain(case, precision="fp64") as d:
+        d.step_dt(dts)
+        eta = d.read("eta")
+        assert rel(eta, o.get("eta")) <= FP64_TOL
+        assert linf(eta, o.get("eta")) <= FP64_LINF
+        got = np.stack([d.read("P"), d.read("Q")])
+        ref = np.stack([o.get("P"), o.get("Q")])
+        assert rel(got, ref) <= FP64_TOL, rel(got, ref)
+        assert linf(got, ref) <= FP64_LINF, linf(got, ref)
+    with bsq.Domain(case, precision="fp32", kahan=True) as d:
+        d.step_dt(dts)
+        assert rel(d.read("eta"), o.get("eta")) <= FP32_TOL
+
+
 def test_tiny_grid_3x3():
     case = _hump_case(3, 3, dx=0.2)
     o = _oracle(case)
