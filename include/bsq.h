@@ -92,9 +92,9 @@ typedef struct {
                               default where its rows fit), bit 4 one warp per row (the
                               single-precision default); [3] rows per warp of the
                               sliding-window RHS (16, 24, 32, 48, 64, 128; 16 selects the
-                              one-column kernel, which takes 24 and 48 as 32, and 128 only
-                              with 8-row chunk summaries formed in the RHS kernel, else 64;
-                              0: by grid size); [4] x-solver elements per thread (4, 8, 16, 32);
+                              one-column kernel, which takes 24 and 48 as 32; 128: 128-row
+                              strips of the one-column kernel where it forms 8-row chunk
+                              summaries itself, else 64; 0: by grid size); [4] x-solver elements per thread (4, 8, 16, 32);
                               [5] rows per y-line chunk (8, 16); [6] bit 0: the chunk
                               summaries by a kernel of their own instead of inside the RHS
                               kernel, bit 1: one column per lane in the single-precision RHS
