@@ -62,8 +62,10 @@ STEP_VALUES = {"fp32": 25, "fp64": 19}
 
 def case_dims(workload, n):
     """Grid of the workload at size n: barred beach n x n, planar beach
-    n x n/4, rip-channel beach n x 3n/2 (1000 x 1500 is the 0.02 m grid)."""
-    return {"barred_beach": (n, n), "planar_beach": (n, max(4, n // 4)), "hamm_rip": (n, 3 * n // 2)}[workload]
+    n x n/4, rip-channel beach n x 3n/2 (1000 x 1500 is the 0.02 m grid),
+    conical island n x n (601 x 601 is the grid of Sec. 5.1)."""
+    return {"barred_beach": (n, n), "planar_beach": (n, max(4, n // 4)), "hamm_rip": (n, 3 * n // 2),
+            "conical_island": (n, n)}[workload]
 
 
 def make_case(workload, n):
@@ -74,6 +76,8 @@ def make_case(workload, n):
         return W.planar_beach(nx=nx, ny=ny)
     if workload == "hamm_rip":
         return W.hamm_rip(nx=nx, ny=ny)
+    if workload == "conical_island":
+        return W.conical_island(nx=nx, ny=ny)
     raise ValueError(workload)
 
 
@@ -784,7 +788,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="barred_beach", choices=["barred_beach", "planar_beach", "hamm_rip"])
+    ap.add_argument("--workload", default="barred_beach",
+                    choices=["barred_beach", "planar_beach", "hamm_rip", "conical_island"])
     ap.add_argument("--n", "--grid", dest="n", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--graph-steps", type=int, default=16)

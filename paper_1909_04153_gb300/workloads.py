@@ -16,7 +16,10 @@ these generators stand in for them with the same kind of geometry and forcing:
   forcing (for many independent domains);
 * ``hamm_rip`` -- a plane beach cut by a rip channel, the analytic bathymetry
   of Eq. 48, irregular JONSWAP waves and quadratic bottom friction (the
-  irregular-wave rip case of Sec. 5.4).
+  irregular-wave rip case of Sec. 5.4);
+* ``conical_island`` -- a solitary wave (H/d = 0.18) running up a conical
+  island in the centre of a square basin, with the geometry Sec. 5.1 states
+  (the solitary run-up case of Sec. 5.1).
 
 Each returns a dict: ``params`` (nx, ny, dx, dy, bc, ...), ``bed`` ((ny+1, nx+1)
 corner elevations, datum = still water level, so ``w_s = 0``), ``comps``
@@ -188,6 +191,31 @@ def hamm_rip(nx=1000, ny=1500, length=20.0, width=30.0, hs=0.13, tp=1.6, gamma=3
     return dict(name="hamm_rip", params=prm, bed=bed, comps=comps, eta0=None, P0=None, Q0=None, steps=steps)
 
 
+def conical_island(nx=601, ny=601, length=30.0, depth=0.32, base_radius=3.6, slope=0.25, amp_ratio=0.18,
+                   x0=3.5, sponge=2.0, steps=7000, **kw):
+    """Solitary wave run-up on a conical island (Sec. 5.1): a length x length
+    basin (30 m, 601 x 601 cells at full size) of depth 0.32 m with an island of
+    7.2 m base diameter and side slope 1/4 at its centre, here a full cone (its
+    top is not given; the peak, 0.58 m above still water, stays dry); a solitary
+    wave of H/d = 0.18 centred x0 from the west side travelling east; sponge
+    layers west and east, walls north and south, no friction.  The paper runs it
+    at CFL 0.145 with a first step of 0.0033 s; the 2D target CFL of this
+    solver (0.125) is the default here."""
+    dx = length / nx
+    dy = length / ny
+    xc, yc, xk, yk = _grid(nx, ny, dx, dy)
+    X, Y = np.meshgrid(xk, yk)
+    r = np.hypot(X - 0.5 * length, Y - 0.5 * length)
+    bed = -depth + np.maximum(base_radius - r, 0.0) * slope
+    eta1, p1 = solitary_profile(xc, x0, amp_ratio * depth, depth)
+    kw.setdefault("cfl", 0.125)
+    kw.setdefault("dt_init", 0.0033)
+    prm = base_params(nx, ny, dx, dy, bc=(SPONGE, SPONGE, WALL, WALL), sponge_width=(sponge, sponge, 0.0, 0.0),
+                      **kw)
+    return dict(name="conical_island", params=prm, bed=bed, comps=None, eta0=np.tile(eta1, (ny, 1)),
+                P0=np.tile(p1, (ny, 1)), Q0=None, steps=steps)
+
+
 def batch_sizes(count=64, lo=128, hi=1024, seed=SEED, multiple=32):
     """Side lengths log-uniform in [lo, hi], rounded to a multiple of 32."""
     rng = np.random.default_rng(seed)
@@ -211,6 +239,7 @@ CASES = {
     "planar_beach": planar_beach,
     "barred_beach": barred_beach,
     "hamm_rip": hamm_rip,
+    "conical_island": conical_island,
 }
 
 

@@ -9,6 +9,8 @@ oracle's dt sequence replayed:
 * the same barred beach on a 512 x 512 grid (same layout, 0.1 m cells), 1000
   steps, the single-precision path against the oracle once the waves have
   grown (no absolute fallback);
+* the conical island of Sec. 5.1, 601 x 601, 200 steps, and an adaptive run
+  through the run-up on the island;
 * the barred beach at 2048 x 2048 for 20,000 steps: single precision with
   compensated accumulation against the double-precision path (which the
   tests above hold to the oracle), the FP64 run's adaptive step sequence
@@ -34,7 +36,8 @@ def _run_oracle(case, steps):
     return o, dts
 
 
-@pytest.mark.parametrize("name,steps", [("solitary_basin", 500), ("planar_beach", 1000), ("barred_beach", 3)])
+@pytest.mark.parametrize("name,steps", [("solitary_basin", 500), ("planar_beach", 1000), ("barred_beach", 3),
+                                        ("conical_island", 200)])
 def test_full_size_parity(name, steps):
     case = W.make(name)
     o, dts = _run_oracle(case, steps)
@@ -69,6 +72,33 @@ def test_full_size_adaptive_run_stays_finite_and_conserves_mass():
         h = d.read("h")
         assert np.isfinite(h).all() and (h >= 0).all()
         assert info["n"] == 400 and info["t"] > 0
+
+
+def test_conical_island_run_up():
+    # the solitary wave of Sec. 5.1 at the paper's 601 x 601 cells, advanced
+    # adaptively for 12 s, sampled every second: it reaches the island (centre
+    # 15 m, still shoreline at radius 2.32 m) after about 5 s and climbs its
+    # west face, then wraps round to the lee face (the oracle on a 301 x 301
+    # grid: front face wet from 5 s, lee face from 7 s); the state stays finite
+    # with h >= 0 throughout
+    case = W.make("conical_island")
+    p = case["params"]
+    n, dx = p["nx"], p["dx"]
+    xc = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(xc, xc)
+    r = np.hypot(X - 15.0, Y - 15.0)
+    dry_at_rest = r < 2.32 - dx
+    lee = dry_at_rest & (X > 15.5)
+    front_wet = lee_wet = 0
+    with bsq.Domain(case, precision="fp32") as d:
+        for T in range(1, 13):
+            d.advance(t_end=float(T))
+            h = d.read("h")
+            assert np.isfinite(h).all() and (h >= 0).all(), T
+            front_wet = max(front_wet, int((h[dry_at_rest] > 1e-3).sum()))
+            lee_wet = max(lee_wet, int((h[lee] > 1e-3).sum()))
+        assert abs(d.info()["t"] - 12.0) <= 1e-9
+    assert front_wet > 100 and lee_wet > 10, (front_wet, lee_wet)
 
 
 def test_hamm_rip_full_size_adaptive_run():

@@ -104,6 +104,7 @@ CASES = {
     "hamm_rip_friction": lambda: W.hamm_rip(nx=100, ny=60),
     "makers_four_sides_oblique": lambda: _maker_case(70, 58, (W.MAKER,) * 4, seed=21),
     "makers_west_east_oblique": lambda: _maker_case(83, 47, (W.MAKER, W.MAKER, W.WALL, W.SPONGE), seed=23),
+    "conical_island": lambda: W.conical_island(nx=121, ny=121),
 }
 
 
@@ -197,7 +198,7 @@ def test_fp64_advance_lands_on_t_end_like_oracle():
 
 @pytest.mark.parametrize("name", ["barred_beach_rips", "hump_2d_walls", "planar_beach_jonswap",
                                   "random_basin_jonswap", "hamm_rip_friction", "makers_four_sides_oblique",
-                                  "makers_west_east_oblique", "tall_solitary_multi_segment"])
+                                  "makers_west_east_oblique", "tall_solitary_multi_segment", "conical_island"])
 def test_fp32_kahan_1000_steps_matches_oracle(name):
     case = CASES[name]()
     o = _oracle(case)

@@ -37,3 +37,31 @@ def test_hamm_rip_case():
     np.testing.assert_allclose(np.diff(comps[:, 1]), 0.01, atol=1e-12)
     # 4 sqrt(m0) = Hs
     assert abs(4.0 * math.sqrt(0.5 * np.sum(comps[:, 0] ** 2)) - 0.13) < 1e-12
+
+
+def test_conical_island_geometry():
+    # Sec. 5.1: 30 m x 30 m basin, 601 x 601 cells, 0.32 m of water, an island of
+    # 7.2 m base diameter and side slope 1/4 at the centre; its still-water
+    # shoreline is then a circle of radius 3.6 - 4 (0.32) = 2.32 m (the radius the
+    # paper scales run-up by); solitary wave of H/d = 0.18; sponges W and E,
+    # walls S and N
+    c = W.conical_island()
+    p = c["params"]
+    assert p["nx"] == 601 and p["ny"] == 601 and abs(p["dx"] * 601 - 30.0) < 1e-12
+    assert p["bc"] == (W.SPONGE, W.SPONGE, W.WALL, W.WALL) and p["friction"] == 0.0
+    bed = c["bed"]
+    xk = np.arange(602) * p["dx"]
+    X, Y = np.meshgrid(xk, xk)
+    r = np.hypot(X - 15.0, Y - 15.0)
+    assert np.all(bed[r >= 3.6] == -0.32)
+    inside = (r < 3.6) & (r > 0.1)
+    np.testing.assert_allclose(bed[inside], -0.32 + (3.6 - r[inside]) / 4.0, atol=1e-14)
+    # the shoreline: bed crosses 0 at r = 2.32 m
+    ring = np.abs(r - 2.32) < 0.5 * p["dx"]
+    assert np.all(np.abs(bed[ring]) <= 0.25 * 0.5 * p["dx"] + 1e-12)
+    # solitary wave: crest 0.18 x 0.32 m, travelling east (P = c eta > 0)
+    assert abs(c["eta0"].max() - 0.18 * 0.32) < 1e-3 * 0.0576
+    assert np.all(c["P0"] >= 0.0) and c["Q0"] is None
+    np.testing.assert_allclose(c["P0"] / np.maximum(c["eta0"], 1e-300),
+                               math.sqrt(9.81 * (0.32 + 0.0576)), rtol=1e-12,
+                               atol=0.0, err_msg="flux = celerity x eta")
