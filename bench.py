@@ -713,8 +713,9 @@ def run_served_only(args):
 
 
 def run_fixed_vs_adaptive(args, dev, stream):
-    """Adaptive against fixed steps on the rip-channel beach of Eq. 48 (JONSWAP
-    waves, friction), FP32: the adaptive run to T gives its mean, smallest and
+    """Adaptive against fixed steps, FP32, on the rip-channel beach of Eq. 48
+    (JONSWAP waves, friction; the default) or the conical island of Sec. 5.1
+    (solitary run-up): the adaptive run to T gives its mean, smallest and
     largest step; fixed-step runs to the same T (cfl = 0, every step dt_init)
     locate, by bisection, the largest fixed step that stays stable (no
     non-finite state, |eta| below 1 m)."""
@@ -724,7 +725,8 @@ def run_fixed_vs_adaptive(args, dev, stream):
 
     n = args.fixed_study_n
     T = args.fixed_study_time
-    case = W.hamm_rip(nx=n, ny=n * 3 // 2)
+    island = args.fixed_study_workload == "conical_island"
+    case = W.conical_island(nx=n, ny=n) if island else W.hamm_rip(nx=n, ny=n * 3 // 2)
     p = case["params"]
     ncell = p["nx"] * p["ny"]
 
@@ -765,8 +767,10 @@ def run_fixed_vs_adaptive(args, dev, stream):
     best = lo if ok_lo else None
     ok_f, steps_f, wall_f = run(cfl=0.0, dt_init=best)[:3] if best else (False, 0, 0.0)
     return {
-        "workload": "rip-channel beach of Eq. 48, %dx%d, dx %.3g m, JONSWAP Hs 0.13 m Tp 1.6 s, friction 0.0025, "
-                    "FP32, %g s simulated" % (p["nx"], p["ny"], p["dx"], T),
+        "workload": ("conical island of Sec. 5.1, %dx%d, dx %.3g m, solitary wave H/d 0.18, FP32, %g s simulated"
+                     % (p["nx"], p["ny"], p["dx"], T)) if island else
+                    ("rip-channel beach of Eq. 48, %dx%d, dx %.3g m, JONSWAP Hs 0.13 m Tp 1.6 s, friction 0.0025, "
+                     "FP32, %g s simulated" % (p["nx"], p["ny"], p["dx"], T)),
         "adaptive": {"steps": steps_a, "mean_dt": mean_dt, "min_dt_sampled": lo_dt, "max_dt_sampled": hi_dt,
                      "cfl": p["cfl"], "wall_s": wall_a, "stable": ok},
         "largest_stable_fixed_dt": best,
@@ -802,6 +806,7 @@ def main(argv=None):
     ap.add_argument("--no-fixed-study", action="store_true")
     ap.add_argument("--fixed-study-n", type=int, default=500)
     ap.add_argument("--fixed-study-time", type=float, default=30.0)
+    ap.add_argument("--fixed-study-workload", default="hamm_rip", choices=["hamm_rip", "conical_island"])
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-time-scale", type=float, default=0.1)
