@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate, beside the rate measured liv
 # DRAM bytes per launch of the dominant kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (kernel, precision, nx, ny); the capture is summarised under profiles/
-MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.867264e6 + 113.133824e6}
+MEASURED_TRAFFIC = {("rhs_combine", "fp32", 2048, 2048): 285.918976e6 + 112.8192e6}
 # algorithmic bytes per interior cell of each kernel (values the method needs it
 # to read and write once: state, bed, compensation terms, history; the
 # right-hand sides dU, dV of the line solves and the stored line factors are
