@@ -1926,7 +1926,9 @@ __device__ __forceinline__ void load_halo_chunk_if(bool pred, const T *row, int 
 // right-hand side (sequential cross form), compensated P update, sponge on w
 // and P, and the Eq. 22 rate of the finished state (one atomic per block).
 template <typename T, int K>
-__global__ void __launch_bounds__(512) k_xsolve(Dev<T> D, double forced_dt_next)
+// (double precision, 4 elements a thread: two rows per multiprocessor at 64
+// registers, so one row's barrier waits overlap the other's FP64 work)
+__global__ void __launch_bounds__(512, (sizeof(T) == 8 && K == 4) ? 2 : 1) k_xsolve(Dev<T> D, double forced_dt_next)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
