@@ -1891,6 +1891,12 @@ __global__ void __launch_bounds__(256) k_yapply(Dev<T> D, int nch, const T *yin,
 {
     yapply_body<T, KY>(D, blockIdx.x, blockIdx.y, nch, yin, xaft);
 }
+// double precision: three blocks per multiprocessor (at most 85 registers)
+template <int KY>
+__global__ void __launch_bounds__(256, 3) k_yapply_d(Dev<double> D, int nch, const double *yin, const double *xaft)
+{
+    yapply_body<double, KY>(D, blockIdx.x, blockIdx.y, nch, yin, xaft);
+}
 
 // ------------------------------------------------------------------ x-line solves
 
@@ -3401,8 +3407,13 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
         // one chunk of 256 adjacent columns per block: each row segment a block
         // reads is 1 KB contiguous
         const dim3 gw((nx + 255) / 256, nch);
-        if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
-        else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        if constexpr (sizeof(T) == 8) {
+            if (KY == 8) k_yapply_d<8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+            else k_yapply_d<16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        } else {
+            if (KY == 8) k_yapply<T, 8><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+            else k_yapply<T, 16><<<gw, dim3(256, 1), 0, st>>>(D, nch, D.yin, D.yxa);
+        }
     }
     if (ev) cudaEventRecord(ev[3], st);
     const int K = x_chunk<T>(nx, D.tune_xk);
