@@ -40,11 +40,11 @@ METRIC = "cell-updates/s"
 # 1 per DADD or DMUL; smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on)
 # and instructions of the FP64 pipe (sm__sass_thread_inst_executed_op_fp64_pred_on),
 # counted with ncu on one launch of each kernel of the double-precision step on
-# the 2048 x 2048 barred beach: RHS 411.8 flops (337.9 instructions), x-line
-# solve 65.7 (53.0), y-line solve 10.8 (8.1), ghost cells 0.1 (summarised under
+# the 2048 x 2048 barred beach: RHS 411.7 flops (337.9 instructions), x-line
+# solve 66.2 (52.6), y-line solve 8.3 (5.6), ghost cells 0.1 (summarised under
 # profiles/)
-FP64_FLOPS_PER_CELL = 488.4
-FP64_INSTR_PER_CELL = 399.1
+FP64_FLOPS_PER_CELL = 486.3
+FP64_INSTR_PER_CELL = 396.2
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate, beside the rate measured live (bsq_fp64_fma_rate)
 # DRAM bytes per launch of the dominant kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
