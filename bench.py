@@ -783,7 +783,10 @@ def run_fixed_vs_adaptive(args, dev, stream):
 
 
 def bsq_bytes_estimate(ncell, fp):
-    return ncell * (31 if fp == "fp32" else 28) * (4 if fp == "fp32" else 8)
+    """Fields a domain holds per cell: FP32 31 (state and Kahan terms 7, history
+    15, line-solve right-hand sides 2, bed 1, line factors 6); FP64 39 (state 4,
+    the same 24, and 11 static terms of the RHS and the x-solver)."""
+    return ncell * (31 if fp == "fp32" else 39) * (4 if fp == "fp32" else 8)
 
 
 def main(argv=None):
