@@ -2651,29 +2651,33 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
     rate = tmax(rate, tmax(mu * D.rdx, mv * D.rdy));
 }
 
-constexpr int XW_WARPS = 4;  // rows (warps) per block of the warp-per-row x-solver
+constexpr int XW_WARPS = 4;  // rows (warps) per block of the batched warp-per-row x-solvers
+// rows (warps) per block of the single-domain warp-per-row x-solver: small
+// blocks spread the rows evenly over the multiprocessors (2048 rows: 13 or 14
+// on each of 152, where blocks of four rows left some with 16)
+constexpr int XW_ONE = 2;
 
 // shared memory of the warp-per-row x-solver: one y row per warp
 template <typename T, int K>
-static size_t xwarp_smem(int nx)
+static size_t xwarp_smem(int nx, int nw = XW_WARPS)
 {
     const int span = 32 * K;
-    return (size_t)XW_WARPS * (size_t)((nx + span - 1) / span) * span * sizeof(T);
+    return (size_t)nw * (size_t)((nx + span - 1) / span) * span * sizeof(T);
 }
 
-// rows blk * XW_WARPS + warp of one domain; the controller of the domain's
-// next step runs in the last of its nparts blocks
-template <typename T, int K, bool FIXED = false>
+// rows blk * NW + warp of one domain; the controller of the domain's next
+// step runs in the last of its nparts blocks
+template <typename T, int K, bool FIXED = false, int NW = XW_WARPS>
 __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsigned nparts, int yrow,
                                                  double forced_dt_next)
 {
     const Coef cf = *D.coef;
     if (!cf.active) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double smax[XW_WARPS];
+    __shared__ double smax[NW];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *ys = reinterpret_cast<T *>(smem_raw) + (size_t)wid * yrow;
-    const int j = blk * XW_WARPS + wid;
+    const int j = blk * NW + wid;
     T rate = (T)0;
     bool bad = false;
     if (j < D.ny) xsolve_row_warp<T, K, FIXED>(D, cf, j, ys, rate, bad);
@@ -2686,7 +2690,7 @@ __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsig
     if (threadIdx.x == 0) {
         double mx = 0.0;
         bool fl = false;
-        for (int q = 0; q < XW_WARPS; q++) {
+        for (int q = 0; q < NW; q++) {
             if (smax[q] < 0.0) fl = true;
             else mx = fmax(mx, smax[q]);
         }
@@ -2697,9 +2701,9 @@ __device__ __forceinline__ void xsolve_warp_body(const Dev<T> &D, int blk, unsig
 }
 
 template <typename T, int K, bool FIXED = false>
-__global__ void __launch_bounds__(32 * XW_WARPS, sizeof(T) == 4 ? 4 : 2) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
+__global__ void __launch_bounds__(32 * XW_ONE, (sizeof(T) == 4 ? 16 : 8) / XW_ONE) k_xsolve_warp(Dev<T> D, int yrow, double forced_dt_next)
 {
-    xsolve_warp_body<T, K, FIXED>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
+    xsolve_warp_body<T, K, FIXED, XW_ONE>(D, blockIdx.x, gridDim.x, yrow, forced_dt_next);
 }
 
 // shared memory bytes of the TMA x-solver for a row span
@@ -3428,16 +3432,16 @@ static cudaError_t step_impl(const Dev<T> &D, cudaStream_t st, double forced_dt_
     }
     if (ev) cudaEventRecord(ev[4], st);
     if (xwarp) {
-        const int xb = (ny + XW_WARPS - 1) / XW_WARPS;
+        const int xb = (ny + XW_ONE - 1) / XW_ONE;
         const bool fixed = D.cross_mode != 0 && D.kahan != 0;
         if (K == 4) {
             const int yrow = (nx + 127) / 128 * 128;
-            if (fixed) k_xsolve_warp<T, 4, true><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
-            else k_xsolve_warp<T, 4><<<xb, 32 * XW_WARPS, xwarp_smem<T, 4>(nx), st>>>(D, yrow, forced_dt_next);
+            if (fixed) k_xsolve_warp<T, 4, true><<<xb, 32 * XW_ONE, xwarp_smem<T, 4>(nx, XW_ONE), st>>>(D, yrow, forced_dt_next);
+            else k_xsolve_warp<T, 4><<<xb, 32 * XW_ONE, xwarp_smem<T, 4>(nx, XW_ONE), st>>>(D, yrow, forced_dt_next);
         } else {
             const int yrow = (nx + 255) / 256 * 256;
-            if (fixed) k_xsolve_warp<T, 8, true><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
-            else k_xsolve_warp<T, 8><<<xb, 32 * XW_WARPS, xwarp_smem<T, 8>(nx), st>>>(D, yrow, forced_dt_next);
+            if (fixed) k_xsolve_warp<T, 8, true><<<xb, 32 * XW_ONE, xwarp_smem<T, 8>(nx, XW_ONE), st>>>(D, yrow, forced_dt_next);
+            else k_xsolve_warp<T, 8><<<xb, 32 * XW_ONE, xwarp_smem<T, 8>(nx, XW_ONE), st>>>(D, yrow, forced_dt_next);
         }
     } else if (pipe) {
         const int grid = min(ny, D.nsm);
