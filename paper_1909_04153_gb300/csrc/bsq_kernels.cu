@@ -2653,7 +2653,7 @@ __device__ __forceinline__ void xsolve_row_warp(const Dev<T> &D, const Coef &cf,
 
 constexpr int XW_WARPS = 4;  // rows (warps) per block of the batched warp-per-row x-solvers
 // rows (warps) per block of the single-domain warp-per-row x-solver: small
-// blocks spread the rows evenly over the multiprocessors (2048 rows: 13 or 14
+// blocks spread the rows evenly over the multiprocessors (2048 rows: 12 or 14
 // on each of 152, where blocks of four rows left some with 16)
 constexpr int XW_ONE = 2;
 
