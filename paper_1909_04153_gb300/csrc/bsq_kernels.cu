@@ -1043,7 +1043,10 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 // double precision reads the static terms set-up formed in the
                 // same order of operations (the same values, bitwise)
                 constexpr bool STAT = sizeof(T) == 8;
-                const T *st = STAT ? D.stat + c : nullptr;
+                // (the first two steps of a strip finish rows below the field's
+                // halo, whose results are dropped: their reads stay in the field)
+                const long long cst = STAT ? fidx(D, i, max(o, -2)) : 0;
+                const T *st = STAT ? D.stat + cst : nullptr;
                 const long long ss = STAT ? D.stat_stride : 0;
                 T srcx, srcy;
                 if constexpr (STAT) {
@@ -1103,7 +1106,7 @@ __device__ __forceinline__ void rhs_sw_body(const Dev<T> &D, int blk, int nstrip
                 T P_xy = (PNp - PSp - PNm + PSm) * q_rdxy;
                 T Fs, Gs;
                 if constexpr (sizeof(T) == 8) {
-                    const T c1 = D.fsc1[c], c2 = D.fsc2[c], c3 = D.fsc3[c];
+                    const T c1 = D.fsc1[cst], c2 = D.fsc2[cst], c3 = D.fsc3[cst];
                     Fs = c1 * Q_y + c2 * Q_x + c3 * Q_xy;
                     Gs = c2 * P_x + c1 * P_y + c3 * P_xy;
                 } else {
